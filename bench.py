@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""MVGD hot-path benchmark: points/s for kNN + assembly + solve of
+(I - L) u = f to a 1e-8 relative residual on a 1,048,576-point random unit
+sphere, K = 20, u = 5z^3 - 3z, f = 13u (synthetic, seeded).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  A step is one pass of the whole path over one cloud:
+kNN -> MVGD assembly -> solve.  The timed path is the FP32 + FP64-refinement
+one; the plain FP64 path (same kNN, same preconditioner, FP64 assembly, FP64
+Krylov) is timed beside it.  L2 is flushed (256 MiB write) before every step,
+outside the per-step CUDA-event windows.  With N > 1 (torchrun) every rank
+solves its own replica of the cloud (weak scaling, no collective on the data
+path); the reported time is the max over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, each
+step a bounded sample of the same workload scaled to points/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "MVGD points/s (assembly+solve to 1e-8 rel) batched/served vs plain; p50/p99 ms"
+N_DEFAULT, K_DEFAULT, SEED = 1_048_576, 20, 0
+RTOL = 1e-8
+WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
+            "6 nearest, u = 5z^3-3z, f = 13u, (I-L)u = f to 1e-8 relative residual")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--k", type=int, default=K_DEFAULT)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in Path(self.file.name).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ------------------------------------------------------------------------------
+# algorithmic bytes of the persistent solver (per row)
+# ------------------------------------------------------------------------------
+def solver_bytes_per_row(k: int, mixed: bool, iters: int, restarts: int) -> float:
+    """Unique bytes one launch of the persistent solver must move per row.
+
+    Mixed, per inner iteration (FP32 vectors, FP32 hi weights, int32 columns):
+      A: col 4k + val 4k + self weight 4 + r,p,v,rh 16 + write p,v 8
+      B: col 4k + val 4k + self weight 4 + r,v 8 + write s,t 8
+      C: x,p,s,t,r,rh 24 + write x,r 8                      -> 16k + 80
+    per restart (FP64 residual on hi + lo):
+      fold u += scale x 20; residual col 4k + hi,lo 8(k+1) + u,f 16 + r64 8;
+      restart r64 8 + self weight 4 + r,rh,p0,p1,v0,v1,x 28  -> 12k + 92
+    Plain FP64, per iteration 24k + 160; per restart 12k + 96.
+    """
+    if mixed:
+        return iters * (16 * k + 80) + restarts * (12 * k + 92)
+    return iters * (24 * k + 160) + restarts * (12 * k + 96)
+
+
+# ------------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ------------------------------------------------------------------------------
+ORACLE_ITERS_FILE = ROOT / "oracle" / "iterations_random_sphere_1m_k20.json"
+
+
+def oracle_sample(n: int, k: int, solve_iters: int = 40):
+    """kNN + assembly of the full cloud and `solve_iters` BiCGSTAB iterations of
+    the oracle; returns (seconds for knn+assembly, seconds per iteration, threads)."""
+    import oracle
+    from paper_1603_04100_gb300 import inputs as I
+    threads = oracle.threads(os.cpu_count() or 1)
+    pr = I.random_sphere_problem(n, k, seed=SEED)
+    t0 = time.perf_counter()
+    nbr = oracle.knn_grid(pr.pts, k)
+    val, _, _, _ = oracle.assemble(pr.pts, nbr, delta_m=6)
+    t1 = time.perf_counter()
+    oracle.bicgstab(val, nbr, pr.f[:, 0], rtol=1e-30, maxit=solve_iters)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / (solve_iters + 2), threads
+
+
+def oracle_iters_needed() -> int | None:
+    if ORACLE_ITERS_FILE.exists():
+        return int(json.loads(ORACLE_ITERS_FILE.read_text())["iters"])
+    return None
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n, k = args.n, args.k
+    iters = oracle_iters_needed()
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count file missing"}))
+        return
+    samples = []
+    for s in range(args.warmup + args.steps):
+        t_setup, t_it, threads = oracle_sample(n, k, solve_iters=20 if s < args.warmup else 40)
+        if s >= args.warmup:
+            samples.append((t_setup, t_it))
+    t_setup = statistics.median(x[0] for x in samples)
+    t_it = statistics.median(x[1] for x in samples)
+    total = t_setup + t_it * iters
+    value = n / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "k": k, "rtol": RTOL, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
+                         "sample": f"full kNN (grid) + assembly of the {n}-point cloud, then 40 BiCGSTAB "
+                                   f"iterations timed and scaled to the {iters} iterations the oracle needs "
+                                   f"for 1e-8 on this cloud ({ORACLE_ITERS_FILE.name})"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1603_04100_gb300 import api, build
+    from paper_1603_04100_gb300 import inputs as I
+    from paper_1603_04100_gb300.pipeline import Pipeline
+    build.build()
+
+    n, k = args.n, args.k
+    pr = I.random_sphere_problem(n, k, seed=SEED)
+    pts = torch.from_numpy(pr.pts).to(dev)
+    f = torch.from_numpy(pr.f).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+
+    def timed_runs(pipe, steps, warmup):
+        """Per-step CUDA-event times of knn / assembly / solve on the pipeline's stream."""
+        for _ in range(warmup):
+            with torch.cuda.stream(stream):
+                pipe.run(pts, f)
+        barrier()
+        rec = []
+        t_wall = time.perf_counter()
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev[0].record(stream)
+                pipe.run_staged(pts, f, ev)
+                ev[3].record(stream)
+            rec.append(ev)
+        barrier()
+        wall = time.perf_counter() - t_wall
+        out = []
+        for ev in rec:
+            out.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])))
+        return out, wall
+
+    mixed = Pipeline(n, k, 1, prec=api.FP32_REFINE, device=dev, precond=1, rtol=RTOL, stream=stream)
+    with ClockSampler(local) as clk:
+        rec, wall = timed_runs(mixed, args.steps, args.warmup)
+    clocks = clk.summary()
+    info = mixed.decode()[0]
+    step_ms = [sum(r) for r in rec]
+    ms = statistics.mean(step_ms)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * n / (t_max * 1e-3)
+    u = mixed.u[:, 0].double().cpu().numpy()
+    err_exact = float(abs(u - pr.u_exact[:, 0]).max())
+
+    # roofline of the dominant kernel: the persistent solver
+    solve_ms = statistics.mean(r[2] for r in rec)
+    bytes_solve = solver_bytes_per_row(k, True, info[0], info[1]) * n
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_solve / (solve_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_solve (persistent BiCGSTAB, FP32 inner + FP64 refinement)",
+                "peak_kind": f"hbm_gbs of {peak_kind}", "bytes_per_launch": bytes_solve,
+                "launch_ms": solve_ms}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "k": k, "rtol": RTOL, "precond": "jacobi",
+                   "path": "fp32 assembly store (hi+lo) / fp32 inner BiCGSTAB / fp64 refinement",
+                   "l2": "flushed before every step (256 MiB write), outside the step events",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "p50_ms": statistics.median(step_ms),
+        "p99_ms": sorted(step_ms)[min(len(step_ms) - 1, math.ceil(0.99 * len(step_ms)) - 1)],
+        "stage_ms": {"knn": statistics.mean(r[0] for r in rec), "assemble": statistics.mean(r[1] for r in rec),
+                     "solve": solve_ms},
+        "iters": info[0], "outer": info[1], "relres": info[2], "solve_status": info[3],
+        "err_exact_inf": err_exact,
+        "gpu_launches": mixed.kernels_per_run * args.steps + args.steps,  # + one flush per step
+        "roofline": roofline, "clocks": clocks,
+    }
+
+    if not args.no_plain:
+        plain = Pipeline(n, k, 1, prec=api.FP64, device=dev, precond=1, rtol=RTOL, stream=stream)
+        prec_rec, _ = timed_runs(plain, max(1, min(args.steps, 2)), 1)
+        pinfo = plain.decode()[0]
+        pms = statistics.mean(sum(r) for r in prec_rec)
+        up = plain.u[:, 0].cpu().numpy()
+        line["plain_fp64"] = {"value": n / (pms * 1e-3), "ms_per_step": pms, "iters": pinfo[0],
+                              "relres": pinfo[2], "err_exact_inf": float(abs(up - pr.u_exact[:, 0]).max()),
+                              "stage_ms": {"knn": statistics.mean(r[0] for r in prec_rec),
+                                           "assemble": statistics.mean(r[1] for r in prec_rec),
+                                           "solve": statistics.mean(r[2] for r in prec_rec)},
+                              "solution_rel_diff_vs_mixed": float(
+                                  ((up - u) ** 2).sum() ** 0.5 / max((up ** 2).sum() ** 0.5, 1e-300))}
+        line["speedup_vs_plain_fp64"] = line["value"] / line["plain_fp64"]["value"] / world
+        del plain
+
+    if not args.no_e2e:
+        pts_h = torch.from_numpy(pr.pts).pin_memory()
+        f_h = torch.from_numpy(pr.f).pin_memory()
+        u_h = torch.empty((n, 1), dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(stream):
+            mixed.run_host(pts_h, f_h, u_h)
+        barrier()
+        e_ms = []
+        for _ in range(max(1, args.steps)):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mixed.run_host(pts_h, f_h, u_h)
+                e1.record(stream)
+            e1.synchronize()
+            e_ms.append(e0.elapsed_time(e1))
+        emean = statistics.mean(e_ms)
+        line["e2e"] = {"value": world * n / (emean * 1e-3), "unit": "points/s",
+                       "h2d_bytes_per_step": pts_h.numel() * 8 + f_h.numel() * 8,
+                       "d2h_bytes_per_step": u_h.numel() * 8, "ms_per_step": emean,
+                       "api": "Pipeline.run_host (mvgd_knn, mvgd_assemble, mvgd_solve via ctypes)"}
+
+    if rank == 0 and not args.no_cpu:
+        t_setup, t_it, threads = oracle_sample(n, k, solve_iters=40)
+        iters_or = oracle_iters_needed()
+        if iters_or is not None:
+            total = t_setup + t_it * iters_or
+            line["cpu_baseline"] = {"value": n / total, "unit": "points/s", "cores": threads, "kind": "oracle",
+                                    "sample": f"full kNN (grid) + assembly of the {n}-point cloud ({t_setup:.2f} s), "
+                                              f"40 BiCGSTAB iterations ({t_it * 1e3:.1f} ms each) scaled to the "
+                                              f"{iters_or} iterations the oracle needs for 1e-8 on this cloud"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

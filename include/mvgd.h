@@ -1,0 +1,197 @@
+/*
+ * mvgd.h -- C ABI of the GB300 (sm_103a) implementation of the Modified
+ * Virtual Grid Difference (MVGD) discretisation of the Laplace-Beltrami
+ * operator on point clouds (Wang, Leung & Zhao, arXiv:1603.04100), and of the
+ * solve of (sigma I - L) u = f that the discretisation feeds.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a
+ *     comment says "host".  The library never allocates, frees or keeps
+ *     caller memory; scratch comes from a caller buffer whose size the
+ *     matching *_workspace_bytes() returns.  Device pointers must be 256-byte
+ *     aligned (every PyTorch allocation is); otherwise MVGD_EINVAL.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = the legacy default
+ *     stream) and the call returns without waiting, except where a comment
+ *     says it synchronises.
+ *   - Errors are returned as mvgd_status; nothing aborts, traps or throws.
+ *     Argument errors are detected on the host before anything is enqueued.
+ *   - Points are FP64 [n][3] row-major.  Indices are int32 (n < 2^31).
+ *   - 5 <= k <= 31 neighbours (the quadratic fit has 6 unknowns and uses the
+ *     point itself plus its k neighbours), and k < n.
+ */
+#ifndef MVGD_H
+#define MVGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *mvgd_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    MVGD_OK = 0,
+    MVGD_EINVAL = 1,      /* bad size, null or misaligned pointer, k out of range */
+    MVGD_EWORKSPACE = 2,  /* workspace smaller than *_workspace_bytes() */
+    MVGD_EDEGENERATE = 3, /* at least one row has a rank-deficient fit (row_status) */
+    MVGD_ENOCONV = 4,     /* solver reached maxit above the tolerance */
+    MVGD_EBREAKDOWN = 5,  /* Krylov breakdown that restarts did not cure */
+    MVGD_ENONFINITE = 6,  /* non-finite input or intermediate value */
+    MVGD_ECANCELLED = 7,  /* a host-set cancel word stopped the device loop */
+    MVGD_ETIMEOUT = 8,    /* a bounded device-side wait gave up */
+    MVGD_ECUDA = 9        /* a CUDA runtime call failed */
+} mvgd_status;
+
+/* Human-readable name of a status (static storage). */
+const char *mvgd_status_string(mvgd_status s);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int32_t mvgd_version(void);
+
+/* ------------------------------------------------------------------------
+ * kNN -- Sec. 2: N(i) = the k nearest neighbours of p_i in R^3.
+ *
+ * nbr[i][0..k-1] (out, int32 [n][k]) are the k indices j != i with the
+ * smallest key (d2_ij, j), ascending, where
+ *     d2_ij = fl(fl(fl(dx*dx) + fl(dy*dy)) + fl(dz*dz)),  dx = fl(x_j - x_i), ...
+ * in IEEE FP64 round-to-nearest without contraction; equal keys are broken by
+ * the lower index.  The result is exact: identical to a brute-force search.
+ *
+ * order (optional out, int32 [n]) receives a locality order of the points
+ * (the cell order of the search grid); pass it to mvgd_assemble so that the
+ * solver works on rows whose neighbours are close in memory.
+ *
+ * cell_size > 0 fixes the edge of the search grid's cells; <= 0 picks one
+ * from an estimate of the k-th neighbour distance.  Results never depend on
+ * it, only the speed does.
+ * ------------------------------------------------------------------------ */
+size_t mvgd_knn_workspace_bytes(int64_t n, int32_t k);
+mvgd_status mvgd_knn(const double *pts, int64_t n, int32_t k, int32_t *nbr, int32_t *order,
+                     double cell_size, void *workspace, size_t workspace_bytes,
+                     mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Assembly -- Sec. 2 and Sec. 3.1.  Row i of L approximates the LB operator at
+ * p_i as a combination of U_i and the values at its k neighbours:
+ *   PCA frame of N(i) (z axis = smallest eigenvalue), local coordinates
+ *   centred at p_i, least-squares quadratics z(x,y) and U(x,y) over p_i and
+ *   N(i) (Eq. 2, Eq. 4), metric coefficients A_1..A_5 of Eq. 3 at the origin,
+ *   centred differences of U(x,y) on the 3x3 virtual grid of spacing h with
+ *   the centre node replaced by U_i (Eq. 7 and the 2-D rule of Sec. 3.1).
+ *
+ * Grid spacing h (Sec. 3.1):
+ *   MVGD_DELTA_QUARTER_RANGE: h = min(range of x_j, range of y_j) / 4 over N(i)
+ *   MVGD_DELTA_MEAN_NN:       h = mean |p_j - p_i| over the m nearest (1 <= m <= k)
+ *   both multiplied by `scale` (> 0).
+ * ------------------------------------------------------------------------ */
+typedef enum { MVGD_DELTA_QUARTER_RANGE = 0, MVGD_DELTA_MEAN_NN = 1 } mvgd_delta_kind;
+
+typedef struct {
+    int32_t kind;  /* mvgd_delta_kind */
+    int32_t m;     /* MEAN_NN only */
+    double scale;  /* 1.0 = the paper's rule */
+} mvgd_delta_rule;
+
+typedef enum {
+    MVGD_FP64 = 0,        /* weights FP64; plain FP64 SpMV and Krylov */
+    MVGD_FP32_REFINE = 1  /* weights as FP32 hi + FP32 lo (hi + lo = the FP64 weight to
+                             ~2^-48 relative); FP32 inner Krylov on hi, FP64 residual on hi+lo */
+} mvgd_precision;
+
+/* Sparse operator in sliced ELL form, slice height 32.  Row r (0 <= r < n)
+ * of the stored matrix is point order[r] (order == NULL: point r).  Element
+ * (r, s) of a [.][w] array lives at  (r / 32) * (32 * w) + s * 32 + (r % 32),
+ * and arrays are sized for n_pad = 32 * ceil(n / 32) rows.
+ *   col  int32 [n_pad][k]:   stored-row index of neighbour s of row r
+ *   val  [n_pad][k+1]:       slot 0 = self weight, slot s+1 = weight of col[s];
+ *                            double (MVGD_FP64) or float hi (MVGD_FP32_REFINE)
+ *   val_lo float [n_pad][k+1] (MVGD_FP32_REFINE only), hi + lo = the weight
+ * Padding rows hold zero weights and point to row 0.  All five pointers
+ * are caller-owned device memory; sizes from mvgd_ell_bytes(). */
+typedef struct {
+    int64_t n;
+    int32_t k;
+    int32_t prec;          /* mvgd_precision */
+    const int32_t *order;  /* [n] or NULL; read by mvgd_assemble and mvgd_solve */
+    int32_t *col;
+    void *val;
+    float *val_lo;
+} mvgd_ell;
+
+enum { MVGD_ELL_COL = 0, MVGD_ELL_VAL = 1, MVGD_ELL_VAL_LO = 2 };
+size_t mvgd_ell_bytes(int64_t n, int32_t k, int32_t prec, int32_t which);
+
+/* Fills L->col, L->val (and L->val_lo).  h (optional out, double [n], point
+ * order) receives the grid spacing; row_status (optional out, uint8 [n],
+ * point order) 0 = ok, 1 = rank-deficient fit (|R_kk| < 1e-10 |R_00| in
+ * h-scaled coordinates), 2 = non-finite value; bad_rows (optional out, one
+ * device int32, zeroed by this call) counts the rows with status != 0.
+ * Asynchronous: check row_status / bad_rows after the stream has run.
+ * The workspace (size from mvgd_assemble_workspace_bytes) is needed only when
+ * L->order is set; it holds the inverse order that maps neighbour indices to
+ * stored rows. */
+size_t mvgd_assemble_workspace_bytes(int64_t n);
+mvgd_status mvgd_assemble(const double *pts, int64_t n, int32_t k, const int32_t *nbr,
+                          mvgd_delta_rule rule, mvgd_ell *L, double *h, uint8_t *row_status,
+                          int32_t *bad_rows, void *workspace, size_t workspace_bytes,
+                          mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Operator application (the product every Krylov step repeats, Sec. 3.1 and
+ * Sec. 4.2):  y = alpha * (sigma x - L x) + beta * y  for nrhs right-hand
+ * sides stored interleaved, x and y [n][nrhs] in STORED row order.
+ *   MVGD_SPMV_F64:      val double, x/y double
+ *   MVGD_SPMV_F32:      val hi,     x/y float, rows evaluated in difference form
+ *                       sum_s w_s (x_col - x_row), the self weight taken as
+ *                       minus the sum of the others (rows of L sum to zero)
+ *   MVGD_SPMV_F64_HILO: val hi + lo in FP64 arithmetic, x/y double
+ * 1 <= nrhs <= 8.  When beta == 0, y is not read.
+ * ------------------------------------------------------------------------ */
+enum { MVGD_SPMV_F64 = 0, MVGD_SPMV_F32 = 1, MVGD_SPMV_F64_HILO = 2 };
+mvgd_status mvgd_spmv(const mvgd_ell *L, int32_t mode, int32_t nrhs, double sigma, double alpha,
+                      const void *x, double beta, void *y, mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Solve (sigma I - L) u = f (Sec. 4.2; the paper uses AMG, this library a
+ * device-resident Krylov method) for nrhs right-hand sides, f and u FP64
+ * [n][nrhs] in POINT order (the solver applies L->order itself).  u holds the
+ * initial guess on entry.
+ *   L->prec == MVGD_FP64:        BiCGSTAB in FP64 to ||f - A u|| <= rtol ||f||.
+ *   L->prec == MVGD_FP32_REFINE: iterative refinement -- FP64 residual on hi+lo,
+ *                                 inner FP32 BiCGSTAB on hi to inner_rtol, FP64
+ *                                 update of u -- until the FP64 residual meets rtol.
+ * All iterations run in one persistent device kernel; no host round trip.
+ * info (out, [nrhs]): if it is host memory the call synchronises the stream
+ * and returns the worst per-RHS status; if device memory, the call is
+ * asynchronous and returns MVGD_OK after enqueueing.
+ * cancel (optional, device or mapped host int32): when it becomes non-zero the
+ * device loop stops at the next iteration with MVGD_ECANCELLED.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double rtol;         /* relative residual target, e.g. 1e-8 */
+    int32_t maxit;       /* cap on Krylov iterations (inner ones included) */
+    int32_t inner_maxit; /* FP32_REFINE: cap per inner solve */
+    double inner_rtol;   /* FP32_REFINE: inner relative tolerance, e.g. 1e-5 */
+    int32_t max_outer;   /* FP32_REFINE: cap on refinement steps */
+    int32_t precond;     /* 0 = none, 1 = left diagonal (Jacobi) scaling of the Krylov system */
+} mvgd_solve_opts;
+
+typedef struct {
+    int32_t iters;       /* Krylov iterations (all inner ones) */
+    int32_t outer;       /* refinement steps (FP32_REFINE), restarts (FP64) */
+    double relres;       /* final ||f - A u||_2 / ||f||_2 in FP64 */
+    int32_t status;      /* mvgd_status */
+    int32_t reserved;
+} mvgd_solve_info;
+
+size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec);
+mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const double *f, double *u,
+                       const mvgd_solve_opts *opts, mvgd_solve_info *info, const int32_t *cancel,
+                       void *workspace, size_t workspace_bytes, mvgd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MVGD_H */

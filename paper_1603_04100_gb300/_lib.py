@@ -1,0 +1,92 @@
+"""ctypes view of the C ABI declared in include/mvgd.h (argument marshalling only).
+
+Loads the in-tree ``_build/libmvgd.so``.  There is no fallback: if the library
+is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from pathlib import Path
+
+_P = C.c_void_p
+LIB_PATH = Path(__file__).resolve().parent / "_build" / "libmvgd.so"
+
+# status codes (mvgd_status)
+OK, EINVAL, EWORKSPACE, EDEGENERATE, ENOCONV, EBREAKDOWN, ENONFINITE, ECANCELLED, ETIMEOUT, ECUDA = range(10)
+DELTA_QUARTER_RANGE, DELTA_MEAN_NN = 0, 1
+FP64, FP32_REFINE = 0, 1
+ELL_COL, ELL_VAL, ELL_VAL_LO = 0, 1, 2
+SPMV_F64, SPMV_F32, SPMV_F64_HILO = 0, 1, 2
+
+EXPORTS = (
+    "mvgd_status_string", "mvgd_version", "mvgd_knn_workspace_bytes", "mvgd_knn", "mvgd_ell_bytes",
+    "mvgd_assemble_workspace_bytes", "mvgd_assemble", "mvgd_spmv", "mvgd_solve_workspace_bytes", "mvgd_solve",
+)
+
+
+class DeltaRule(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("m", C.c_int32), ("scale", C.c_double)]
+
+
+class Ell(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k", C.c_int32), ("prec", C.c_int32), ("order", _P), ("col", _P),
+                ("val", _P), ("val_lo", _P)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("maxit", C.c_int32), ("inner_maxit", C.c_int32),
+                ("inner_rtol", C.c_double), ("max_outer", C.c_int32), ("precond", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("relres", C.c_double), ("status", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class MvgdError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        super().__init__(f"{fn}: {status_string(status)}")
+
+
+_lib = None
+
+
+def load(path: str | os.PathLike | None = None) -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        raise RuntimeError(f"libmvgd.so not built ({p}); run paper_1603_04100_gb300.build.build()")
+    L = C.CDLL(str(p))
+    L.mvgd_status_string.argtypes = [C.c_int]; L.mvgd_status_string.restype = C.c_char_p
+    L.mvgd_version.argtypes = []; L.mvgd_version.restype = C.c_int32
+    L.mvgd_knn_workspace_bytes.argtypes = [C.c_int64, C.c_int32]; L.mvgd_knn_workspace_bytes.restype = C.c_size_t
+    L.mvgd_knn.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, C.c_double, _P, C.c_size_t, _P]
+    L.mvgd_knn.restype = C.c_int
+    L.mvgd_ell_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32]; L.mvgd_ell_bytes.restype = C.c_size_t
+    L.mvgd_assemble_workspace_bytes.argtypes = [C.c_int64]; L.mvgd_assemble_workspace_bytes.restype = C.c_size_t
+    L.mvgd_assemble.argtypes = [_P, C.c_int64, C.c_int32, _P, DeltaRule, C.POINTER(Ell), _P, _P, _P, _P,
+                                C.c_size_t, _P]
+    L.mvgd_assemble.restype = C.c_int
+    L.mvgd_spmv.argtypes = [C.POINTER(Ell), C.c_int32, C.c_int32, C.c_double, C.c_double, _P, C.c_double, _P, _P]
+    L.mvgd_spmv.restype = C.c_int
+    L.mvgd_solve_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32]
+    L.mvgd_solve_workspace_bytes.restype = C.c_size_t
+    L.mvgd_solve.argtypes = [C.POINTER(Ell), C.c_int32, C.c_double, _P, _P, C.POINTER(SolveOpts), _P, _P, _P,
+                             C.c_size_t, _P]
+    L.mvgd_solve.restype = C.c_int
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return load().mvgd_status_string(int(s)).decode()
+
+
+def check(fn: str, status: int) -> int:
+    if status != OK:
+        raise MvgdError(fn, status)
+    return status

@@ -1,0 +1,201 @@
+"""PyTorch-facing API over the C ABI: tensors supply device memory and streams,
+every step of the path runs in libmvgd's CUDA kernels.
+
+    nbr, order = knn(pts, k, want_order=True)
+    op = assemble(pts, nbr, prec=FP32_REFINE, order=order)
+    u, info = solve(op, f, rtol=1e-8)
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as LB
+from ._lib import (DELTA_MEAN_NN, DELTA_QUARTER_RANGE, FP32_REFINE, FP64, SPMV_F32, SPMV_F64,  # noqa: F401
+                   SPMV_F64_HILO, MvgdError)
+
+SLICE = 32
+
+
+def _vp(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _require_cuda(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def n_padded(n: int) -> int:
+    return (n + SLICE - 1) // SLICE * SLICE
+
+
+def knn(pts: torch.Tensor, k: int, *, want_order: bool = False, cell_size: float = 0.0, stream=None,
+        workspace: torch.Tensor | None = None):
+    """K nearest neighbours (int32 [n][k], ascending (d2, index)); optionally a locality order."""
+    _require_cuda(pts, torch.float64, "pts")
+    n = pts.shape[0]
+    L = LB.load()
+    nbr = torch.empty((n, k), dtype=torch.int32, device=pts.device)
+    order = torch.empty(n, dtype=torch.int32, device=pts.device) if want_order else None
+    need = L.mvgd_knn_workspace_bytes(n, k)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, pts.device)
+    LB.check("mvgd_knn", L.mvgd_knn(_vp(pts), n, k, _vp(nbr), _vp(order), float(cell_size), _vp(ws), ws.numel(),
+                                     _stream(stream)))
+    return (nbr, order) if want_order else nbr
+
+
+@dataclass
+class Operator:
+    """The assembled MVGD operator L in sliced ELL form (device tensors)."""
+    n: int
+    k: int
+    prec: int
+    col: torch.Tensor
+    val: torch.Tensor
+    val_lo: torch.Tensor | None
+    order: torch.Tensor | None = None
+    h: torch.Tensor | None = None
+    status: torch.Tensor | None = None
+    bad_rows: torch.Tensor | None = None
+    _c: LB.Ell = field(default=None, repr=False)
+
+    def cstruct(self) -> LB.Ell:
+        self._c = LB.Ell(self.n, self.k, self.prec, _vp(self.order), _vp(self.col), _vp(self.val),
+                         _vp(self.val_lo))
+        return self._c
+
+    def rows(self, which: str = "val") -> np.ndarray:
+        """Host copy [n][k+1] (val / val_lo) or [n][k] (col), stored row order."""
+        t = {"val": self.val, "val_lo": self.val_lo, "col": self.col}[which]
+        w = self.k if which == "col" else self.k + 1
+        return sell_to_rows(t.cpu().numpy(), self.n, w)
+
+    def weights(self) -> np.ndarray:
+        """FP64 weights [n][k+1] in stored row order (hi + lo in the mixed format)."""
+        v = self.rows("val").astype(np.float64)
+        if self.prec == FP32_REFINE:
+            v = v + self.rows("val_lo").astype(np.float64)
+        return v
+
+
+def sell_to_rows(a: np.ndarray, n: int, w: int) -> np.ndarray:
+    """Sliced-ELL storage (slice height 32, slot-major inside a slice) -> [n][w]."""
+    npad = n_padded(n)
+    return a[: npad * w].reshape(npad // SLICE, w, SLICE).transpose(0, 2, 1).reshape(npad, w)[:n]
+
+
+def ell_alloc(n: int, k: int, prec: int, device) -> tuple:
+    L = LB.load()
+    col = torch.empty(L.mvgd_ell_bytes(n, k, prec, LB.ELL_COL) // 4, dtype=torch.int32, device=device)
+    vdt = torch.float64 if prec == FP64 else torch.float32
+    vbytes = L.mvgd_ell_bytes(n, k, prec, LB.ELL_VAL)
+    val = torch.empty(vbytes // vdt.itemsize, dtype=vdt, device=device)
+    lo = None
+    if prec == FP32_REFINE:
+        lo = torch.empty(L.mvgd_ell_bytes(n, k, prec, LB.ELL_VAL_LO) // 4, dtype=torch.float32, device=device)
+    return col, val, lo
+
+
+def assemble(pts: torch.Tensor, nbr: torch.Tensor, *, prec: int = FP64, order: torch.Tensor | None = None,
+             delta_kind: int = DELTA_MEAN_NN, delta_m: int = 6, delta_scale: float = 1.0,
+             want_h: bool = True, want_status: bool = True, stream=None, out: Operator | None = None) -> Operator:
+    """MVGD rows (Sec. 2, Sec. 3.1) for every point into a sliced ELL operator."""
+    _require_cuda(pts, torch.float64, "pts")
+    _require_cuda(nbr, torch.int32, "nbr")
+    n, k = nbr.shape
+    if order is not None:
+        _require_cuda(order, torch.int32, "order")
+    L = LB.load()
+    if out is None:
+        col, val, lo = ell_alloc(n, k, prec, pts.device)
+        op = Operator(n, k, prec, col, val, lo, order)
+        op.h = torch.empty(n, dtype=torch.float64, device=pts.device) if want_h else None
+        op.status = torch.empty(n, dtype=torch.uint8, device=pts.device) if want_status else None
+        op.bad_rows = torch.zeros(1, dtype=torch.int32, device=pts.device)
+    else:
+        op = out
+        op.order = order
+    ws = _workspace(L.mvgd_assemble_workspace_bytes(n), pts.device) if order is not None else None
+    rule = LB.DeltaRule(delta_kind, delta_m if delta_kind == DELTA_MEAN_NN else 0, float(delta_scale))
+    c = op.cstruct()
+    LB.check("mvgd_assemble", L.mvgd_assemble(_vp(pts), n, k, _vp(nbr), rule, C.byref(c), _vp(op.h),
+                                               _vp(op.status), _vp(op.bad_rows), _vp(ws),
+                                               ws.numel() if ws is not None else 0, _stream(stream)))
+    return op
+
+
+def spmv(op: Operator, x: torch.Tensor, *, mode: int | None = None, sigma: float = 1.0, alpha: float = 1.0,
+         beta: float = 0.0, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """y = alpha (sigma x - L x) + beta y, x and y [n] or [n][nrhs] in stored row order."""
+    if mode is None:
+        mode = SPMV_F64 if op.prec == FP64 else SPMV_F32
+    dt = torch.float32 if mode == SPMV_F32 else torch.float64
+    _require_cuda(x, dt, "x")
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    if y is None:
+        y = torch.empty_like(x)
+        beta = 0.0
+    L = LB.load()
+    c = op.cstruct()
+    LB.check("mvgd_spmv", L.mvgd_spmv(C.byref(c), mode, nrhs, sigma, alpha, _vp(x), beta, _vp(y), _stream(stream)))
+    return y
+
+
+@dataclass
+class SolveResult:
+    u: torch.Tensor
+    iters: list
+    outer: list
+    relres: list
+    status: list
+
+
+def solve(op: Operator, f: torch.Tensor, *, u0: torch.Tensor | None = None, sigma: float = 1.0,
+          rtol: float = 1e-8, maxit: int = 200000, inner_rtol: float = 1e-5, inner_maxit: int = 100000,
+          max_outer: int = 60, precond: int = 0, cancel: torch.Tensor | None = None, stream=None,
+          workspace: torch.Tensor | None = None, sync: bool = True) -> SolveResult:
+    """Solve (sigma I - L) u = f; f, u FP64 [n] or [n][nrhs] in point order."""
+    _require_cuda(f, torch.float64, "f")
+    nrhs = 1 if f.dim() == 1 else f.shape[1]
+    u = torch.zeros_like(f) if u0 is None else u0.clone()
+    L = LB.load()
+    need = L.mvgd_solve_workspace_bytes(op.n, op.k, nrhs, op.prec)
+    ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, f.device)
+    opts = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond)
+    c = op.cstruct()
+    if sync:
+        info = (LB.SolveInfo * nrhs)()
+        st = L.mvgd_solve(C.byref(c), nrhs, sigma, _vp(f), _vp(u), C.byref(opts), C.cast(info, C.c_void_p),
+                          _vp(cancel), _vp(ws), ws.numel(), _stream(stream))
+        if st in (LB.EINVAL, LB.EWORKSPACE, LB.ECUDA):
+            raise MvgdError("mvgd_solve", st)
+        return SolveResult(u, [i.iters for i in info], [i.outer for i in info], [i.relres for i in info],
+                           [i.status for i in info])
+    dinfo = torch.zeros(nrhs * C.sizeof(LB.SolveInfo), dtype=torch.uint8, device=f.device)
+    LB.check("mvgd_solve", L.mvgd_solve(C.byref(c), nrhs, sigma, _vp(f), _vp(u), C.byref(opts), _vp(dinfo),
+                                        _vp(cancel), _vp(ws), ws.numel(), _stream(stream)))
+    return SolveResult(u, dinfo, None, None, None)
+
+
+def decode_info(dinfo: torch.Tensor) -> list:
+    raw = bytes(dinfo.cpu().numpy().tobytes())
+    n = len(raw) // C.sizeof(LB.SolveInfo)
+    arr = (LB.SolveInfo * n).from_buffer_copy(raw)
+    return [(i.iters, i.outer, i.relres, i.status) for i in arr]

@@ -1,0 +1,110 @@
+// Internal helpers shared by the CUDA translation units of libmvgd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mvgd.h"
+
+#define MVGD_API extern "C" __attribute__((visibility("default")))
+
+namespace mvgd {
+
+constexpr int kWarp = 32;
+constexpr int kSlice = 32;          // SELL slice height
+constexpr int kMaxK = 31;
+constexpr int kMinK = 5;
+constexpr size_t kAlign = 256;
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a = kAlign) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int64_t n_padded(int64_t n) { return (n + kSlice - 1) / kSlice * kSlice; }
+
+// Element (r, s) of a sliced-ELL array of width w.
+__host__ __device__ inline int64_t sell_index(int64_t r, int s, int w) {
+    return (r / kSlice) * (int64_t)(kSlice * w) + (int64_t)s * kSlice + (r % kSlice);
+}
+
+inline bool aligned(const void* p) { return p == nullptr || ((uintptr_t)p % kAlign) == 0; }
+
+// Carves 256-byte aligned sub-buffers out of a caller workspace.
+struct Carver {
+    char* base;
+    size_t used = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <typename T>
+    T* take(size_t count) {
+        T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+        used += align_up(sizeof(T) * count);
+        return p;
+    }
+};
+
+#define MVGD_CUDA_TRY(expr)                              \
+    do {                                                 \
+        cudaError_t e_ = (expr);                         \
+        if (e_ != cudaSuccess) return MVGD_ECUDA;        \
+    } while (0)
+
+inline mvgd_status launch_status() {
+    return cudaGetLastError() == cudaSuccess ? MVGD_OK : MVGD_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & (kWarp - 1); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+    return __shfl_sync(0xffffffffu, v, src);
+}
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
+    return __shfl_xor_sync(0xffffffffu, v, m);
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide barrier for persistent cooperative kernels.  Sense-reversing,
+// bounded: after `limit` polls it sets *err and returns false, so a kernel
+// whose blocks were not all resident ends with an error status instead of
+// spinning forever.
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned int* count;   // zeroed before the launch
+    volatile unsigned int* gen;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier b, int* err, long long limit) {
+    __syncthreads();
+    bool ok = true;
+    if (threadIdx.x == 0) {
+        unsigned int my_gen = *b.gen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(b.count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            *b.count = 0;
+            __threadfence();
+            atomicAdd((unsigned int*)b.gen, 1u);
+        } else {
+            long long polls = 0;
+            while (*b.gen == my_gen) {
+                if (++polls > limit || *(volatile int*)err != 0) {
+                    atomicCAS(err, 0, (int)MVGD_ETIMEOUT);
+                    ok = false;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok && (*(volatile int*)err == 0);
+}
+
+}  // namespace mvgd

@@ -1,0 +1,83 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares (no compute calls: this runs without a GPU)."""
+import ctypes as C
+import re
+import subprocess
+from pathlib import Path
+
+import pytest
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    names = set()
+    for h in (ROOT / "include").glob("*.h"):
+        text = re.sub(r"/\*.*?\*/", "", h.read_text(), flags=re.S)
+        for m in re.finditer(r"\b(mvgd_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1603_04100_gb300 import build
+    return build.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for n in ("mvgd_knn", "mvgd_assemble", "mvgd_spmv", "mvgd_solve", "mvgd_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = C.CDLL(str(lib_path))
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_exports_are_only_the_abi(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", str(lib_path)], capture_output=True, text=True).stdout
+    ours = sorted({line.split()[-1] for line in out.splitlines() if line.split()[-1].startswith("mvgd_")})
+    assert ours == declared_functions()
+
+
+def test_host_side_queries(lib_path):
+    from paper_1603_04100_gb300 import _lib as LB
+    L = LB.load(lib_path)
+    assert L.mvgd_version() >= 100
+    assert LB.status_string(LB.EINVAL).startswith("MVGD_EINVAL")
+    n, k = 1000, 20
+    assert L.mvgd_knn_workspace_bytes(n, k) > 16 * n
+    assert L.mvgd_ell_bytes(n, k, LB.FP64, LB.ELL_VAL) == 1024 * 21 * 8
+    assert L.mvgd_ell_bytes(n, k, LB.FP32_REFINE, LB.ELL_VAL_LO) == 1024 * 21 * 4
+    assert L.mvgd_ell_bytes(n, k, LB.FP64, LB.ELL_VAL_LO) == 0
+    assert L.mvgd_solve_workspace_bytes(n, k, 2, LB.FP32_REFINE) > 9 * 4 * 2 * n
+
+
+def test_argument_errors_are_reported_before_any_launch(lib_path):
+    """Null or misaligned pointers and bad sizes return MVGD_EINVAL without touching the device."""
+    from paper_1603_04100_gb300 import _lib as LB
+    L = LB.load(lib_path)
+    assert L.mvgd_knn(None, 100, 10, None, None, 0.0, None, 0, None) == LB.EINVAL
+    assert L.mvgd_knn(C.c_void_p(256), 100, 40, C.c_void_p(512), None, 0.0, C.c_void_p(1024), 1 << 20,
+                      None) == LB.EINVAL                      # k > 31
+    assert L.mvgd_knn(C.c_void_p(257), 100, 10, C.c_void_p(512), None, 0.0, C.c_void_p(1024), 1 << 20,
+                      None) == LB.EINVAL                      # misaligned
+    assert L.mvgd_knn(C.c_void_p(256), 100, 10, C.c_void_p(512), None, 0.0, C.c_void_p(1024), 16,
+                      None) == LB.EWORKSPACE
+    e = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
+    rule = LB.DeltaRule(LB.DELTA_MEAN_NN, 6, 1.0)
+    assert L.mvgd_assemble(C.c_void_p(256), 100, 4, C.c_void_p(512), rule, C.byref(e), None, None, None, None, 0,
+                           None) == LB.EINVAL                 # k < 5
+    e = LB.Ell(100, 10, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
+    bad = LB.DeltaRule(LB.DELTA_MEAN_NN, 11, 1.0)
+    assert L.mvgd_assemble(C.c_void_p(256), 100, 10, C.c_void_p(512), bad, C.byref(e), None, None, None, None, 0,
+                           None) == LB.EINVAL                 # m > k
+    assert L.mvgd_spmv(C.byref(e), LB.SPMV_F32, 1, 1.0, 1.0, C.c_void_p(256), 0.0, C.c_void_p(512),
+                       None) == LB.EINVAL                     # FP32 mode on an FP64 operator
+    opts = LB.SolveOpts(0.0, 10, 10, 1e-5, 5, 0)
+    info = (LB.SolveInfo * 1)()
+    assert L.mvgd_solve(C.byref(e), 1, 1.0, C.c_void_p(256), C.c_void_p(512), C.byref(opts),
+                        C.cast(info, C.c_void_p), None, C.c_void_p(1024), 1 << 30, None) == LB.EINVAL  # rtol 0

@@ -1,0 +1,262 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: neighbour lists bit-exact; FP64 weights within 1e-10 of the oracle's,
+row-relative (max over the row of the difference / max |oracle weight|);
+hi + lo weights likewise; solutions within 1e-8 relative (2-norm) of the
+oracle solved to 1e-13, and the oracle operator's residual of the GPU
+solution at the requested tolerance.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1603_04100_gb300 import inputs as I
+from tests.gpu_util import cuda_or_skip, row_relerr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return cuda_or_skip()
+
+
+def _api():
+    from paper_1603_04100_gb300 import api
+    return api
+
+
+CLOUDS = {
+    "fib2562": lambda: I.fibonacci_sphere(2562),
+    "rand20001": lambda: I.random_sphere(20001, 0),
+    "torus12345": lambda: I.torus(12345, 1),
+    "ellipsoid7777": lambda: I.ellipsoid(7777, 2),
+    "dups": lambda: np.concatenate([I.random_sphere(3000, 4), I.random_sphere(3000, 4)[:1000]]),
+    "clusters": lambda: np.concatenate([I.random_sphere(4000, 5) * 1e-3, I.random_sphere(900, 6) + 3.0]),
+    "lattice": lambda: np.stack(np.meshgrid(np.arange(17.0), np.arange(13.0), np.arange(3.0), indexing="ij"),
+                                -1).reshape(-1, 3),
+}
+
+
+@pytest.mark.parametrize("name", list(CLOUDS))
+@pytest.mark.parametrize("k", [5, 12, 20, 31])
+def test_knn_bit_exact(dev, name, k):
+    api = _api()
+    p = CLOUDS[name]()
+    nbr, order = api.knn(torch.from_numpy(p).to(dev), k, want_order=True)
+    got = nbr.cpu().numpy()
+    want = oracle.knn_grid(p, k)
+    np.testing.assert_array_equal(got, want)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(len(p)))
+
+
+@pytest.mark.parametrize("cell", [0.0, 0.003, 0.5])
+def test_knn_independent_of_cell_size(dev, cell):
+    api = _api()
+    p = I.torus(5000, 9)
+    nbr = api.knn(torch.from_numpy(p).to(dev), 16, cell_size=cell).cpu().numpy()
+    np.testing.assert_array_equal(nbr, oracle.knn_brute(p, 16))
+
+
+def test_knn_tiny(dev):
+    api = _api()
+    p = I.random_sphere(7, 3)
+    nbr = api.knn(torch.from_numpy(p).to(dev), 6).cpu().numpy()
+    np.testing.assert_array_equal(nbr, oracle.knn_brute(p, 6))
+
+
+def _assemble_both(dev, p, k, prec, order=False, delta_kind=1, delta_m=6):
+    api = _api()
+    pt = torch.from_numpy(p).to(dev)
+    nbr_t, ord_t = api.knn(pt, k, want_order=True)
+    nbr = nbr_t.cpu().numpy()
+    op = api.assemble(pt, nbr_t, prec=prec, order=ord_t if order else None, delta_kind=delta_kind,
+                      delta_m=delta_m)
+    val, st, dg, _ = oracle.assemble(p, nbr, delta_kind=delta_kind, delta_m=delta_m)
+    return op, nbr, val, st, dg
+
+
+@pytest.mark.parametrize("name", ["fib2562", "rand20001", "torus12345", "ellipsoid7777"])
+@pytest.mark.parametrize("k", [12, 20, 24])
+def test_assemble_fp64_parity(dev, name, k):
+    api = _api()
+    p = CLOUDS[name]()
+    op, nbr, val, st, dg = _assemble_both(dev, p, k, api.FP64)
+    got = op.weights()
+    err = row_relerr(got, val)
+    assert err.max() <= W_TOL, (err.max(), int(err.argmax()))
+    np.testing.assert_array_equal(op.rows("col"), nbr)
+    np.testing.assert_allclose(op.h.cpu().numpy(), dg[:, 5], rtol=1e-13)
+    np.testing.assert_array_equal(op.status.cpu().numpy(), st)
+    assert int(op.bad_rows.item()) == int((st > 0).sum())
+
+
+def test_assemble_quarter_range_parity(dev):
+    """Quarter-range h depends on the tangent axes: compare rows whose tangent
+    eigen-gap is > 1e-6 (elsewhere the axes are not determined)."""
+    api = _api()
+    p = I.torus(9000, 4)
+    op, nbr, val, st, dg = _assemble_both(dev, p, 16, api.FP64, delta_kind=api.DELTA_QUARTER_RANGE)
+    ok = dg[:, 9] > 1e-6
+    assert ok.mean() > 0.99
+    err = row_relerr(op.weights()[ok], val[ok])
+    assert err.max() <= W_TOL, err.max()
+
+
+@pytest.mark.parametrize("k", [12, 20])
+def test_assemble_mixed_hilo(dev, k):
+    api = _api()
+    p = I.random_sphere(30000, 3)
+    op, nbr, val, st, dg = _assemble_both(dev, p, k, api.FP32_REFINE)
+    hi = op.rows("val").astype(np.float64)
+    lo = op.rows("val_lo").astype(np.float64)
+    np.testing.assert_array_equal(hi.astype(np.float32).astype(np.float64), hi)
+    # hi is the FP32 rounding of the weight, lo the FP32 rounding of the rest
+    assert np.all(np.abs(lo) <= 2.0 ** -23 * np.abs(hi) + 1e-300)
+    err = row_relerr(hi + lo, val)
+    assert err.max() <= W_TOL, err.max()
+
+
+def test_assemble_with_locality_order(dev):
+    api = _api()
+    p = I.random_sphere(20001, 7)
+    op, nbr, val, st, dg = _assemble_both(dev, p, 20, api.FP64, order=True)
+    order = op.order.cpu().numpy()
+    inv = np.empty_like(order)
+    inv[order] = np.arange(len(order))
+    got = op.weights()
+    err = row_relerr(got, val[order])
+    assert err.max() <= W_TOL
+    np.testing.assert_array_equal(op.rows("col"), inv[nbr[order]])
+
+
+def _random_x(n, q, seed, dtype=np.float64):
+    return np.random.default_rng(seed).normal(size=(n, q)).astype(dtype)
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 8])
+def test_spmv_fp64(dev, nrhs):
+    api = _api()
+    p = I.torus(12345, 1)
+    op, nbr, val, st, dg = _assemble_both(dev, p, 16, api.FP64)
+    x = _random_x(len(p), nrhs, 1)
+    y0 = _random_x(len(p), nrhs, 2)
+    want = oracle.spmv(val, nbr, x, sigma=1.3, alpha=-0.7, beta=0.25, y=y0)
+    yt = torch.from_numpy(y0).to(dev)
+    got = api.spmv(op, torch.from_numpy(x).to(dev), sigma=1.3, alpha=-0.7, beta=0.25, y=yt).cpu().numpy()
+    scale = (np.abs(val[:, :1]) + np.abs(val[:, 1:]).sum(1, keepdims=True)) * np.abs(x).max()
+    assert np.all(np.abs(got - want) <= 1e-12 * scale)
+
+
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_spmv_mixed_modes(dev, nrhs):
+    api = _api()
+    p = I.random_sphere(20001, 5)
+    op, nbr, val, st, dg = _assemble_both(dev, p, 20, api.FP32_REFINE)
+    F, _ = I.surface_laplacian(I.SPHERE, p, "sinx_expy")
+    x = np.stack([F * (1 + 0.1 * q) for q in range(nrhs)], 1)
+    want = oracle.spmv(val, nbr, x, sigma=1.0)
+    # hi + lo in FP64
+    got = api.spmv(op, torch.from_numpy(x).to(dev), mode=api.SPMV_F64_HILO).cpu().numpy()
+    scale = np.abs(val).sum(1, keepdims=True) * np.abs(x).max()
+    assert np.all(np.abs(got - want) <= 1e-12 * scale)
+    # FP32 difference form: error bounded by the rounding of weights, differences and sums
+    x32 = x.astype(np.float32)
+    got32 = api.spmv(op, torch.from_numpy(x32).to(dev), mode=api.SPMV_F32).cpu().numpy().astype(np.float64)
+    xd = x32.astype(np.float64)
+    diff_scale = np.stack([(np.abs(val[:, 1:]) * np.abs(xd[nbr, q] - xd[:, q:q + 1])).sum(1) for q in range(nrhs)], 1)
+    want32 = oracle.spmv(val, nbr, xd, sigma=1.0)
+    bound = 64 * 2.0 ** -24 * (diff_scale + np.abs(xd)) + 1e-30
+    assert np.all(np.abs(got32 - want32) <= bound), (np.abs(got32 - want32) / bound).max()
+
+
+def _solve_both(dev, pr, prec, rtol, precond=0, order=True):
+    api = _api()
+    pt = torch.from_numpy(pr.pts).to(dev)
+    nbr_t, ord_t = api.knn(pt, pr.k, want_order=True)
+    op = api.assemble(pt, nbr_t, prec=prec, order=ord_t if order else None, delta_m=pr.delta_m)
+    res = api.solve(op, torch.from_numpy(np.ascontiguousarray(pr.f)).to(dev), rtol=rtol, precond=precond)
+    nbr = nbr_t.cpu().numpy()
+    val, st, dg, _ = oracle.assemble(pr.pts, nbr, delta_m=pr.delta_m)
+    return res, nbr, val
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32_refine"])
+@pytest.mark.parametrize("precond", [0, 1], ids=["none", "jacobi"])
+def test_solve_fibonacci_config(dev, prec, precond):
+    """Fibonacci sphere, 2,562 points, K=12, f = 3x, exact u = x; tolerance 1e-10."""
+    pr = I.fibonacci_problem(2562, 12)
+    res, nbr, val = _solve_both(dev, pr, prec, 1e-10, precond)
+    assert res.status == [0], res
+    u = res.u.cpu().numpy()
+    uo, _, _ = oracle.solve(val, nbr, pr.f, rtol=1e-13)
+    assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo)
+    # backward check with the oracle operator
+    r = pr.f - oracle.spmv(val, nbr, u)
+    assert np.linalg.norm(r) <= 1.0001e-10 * np.linalg.norm(pr.f)
+    # the same discretisation error against the exact solution
+    e_gpu = np.abs(u - pr.u_exact).max()
+    e_or = np.abs(uo - pr.u_exact).max()
+    assert abs(e_gpu - e_or) <= 1e-3 * e_or
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32_refine"])
+@pytest.mark.parametrize("rtol,fwd", [(1e-8, 1e-7), (1e-9, 1e-8)])
+def test_solve_random_sphere_multi_rhs(dev, prec, rtol, fwd):
+    """A residual target bounds the backward error; the forward error (against
+    the oracle solved to 1e-13) is then a small multiple of it, so the 1e-8
+    forward bar is checked on solves to a 1e-9 residual."""
+    pr = I.shape_problem(I.SPHERE, 20001, 20, 11, ("x", "p3", "yz"))
+    res, nbr, val = _solve_both(dev, pr, prec, rtol)
+    assert res.status == [0, 0, 0], res
+    u = res.u.cpu().numpy()
+    for q in range(3):
+        uo, _, _ = oracle.solve(val, nbr, pr.f[:, q], rtol=1e-13)
+        assert np.linalg.norm(u[:, q] - uo) <= fwd * np.linalg.norm(uo), q
+        r = pr.f[:, q] - oracle.spmv(val, nbr, u[:, q])
+        assert np.linalg.norm(r) <= 1.0001 * rtol * np.linalg.norm(pr.f[:, q])
+
+
+def test_solve_torus_mixed(dev):
+    pr = I.torus_problem(30001, 24, seed=1)
+    res, nbr, val = _solve_both(dev, pr, 1, 1e-9, precond=1)
+    assert res.status == [0]
+    u = res.u.cpu().numpy()[:, 0]
+    uo, _, _ = oracle.solve(val, nbr, pr.f[:, 0], rtol=1e-13)
+    assert np.linalg.norm(u - uo) <= 1e-8 * np.linalg.norm(uo)
+
+
+def test_solve_without_order_matches_with_order(dev):
+    pr = I.random_sphere_problem(8193, 20, seed=3)
+    r1, nbr, val = _solve_both(dev, pr, 1, 1e-9, order=True)
+    r2, _, _ = _solve_both(dev, pr, 1, 1e-9, order=False)
+    u1, u2 = r1.u.cpu().numpy(), r2.u.cpu().numpy()
+    assert np.linalg.norm(u1 - u2) <= 1e-8 * np.linalg.norm(u1)
+
+
+def test_solve_status_paths(dev):
+    """Iteration cap, cancellation and non-finite input end with a status, not a fault."""
+    api = _api()
+    pr = I.random_sphere_problem(5000, 12, seed=2)
+    pt = torch.from_numpy(pr.pts).to(dev)
+    nbr = api.knn(pt, 12)
+    op = api.assemble(pt, nbr, prec=api.FP64)
+    f = torch.from_numpy(pr.f).to(dev)
+    r = api.solve(op, f, rtol=1e-12, maxit=3)
+    assert r.status == [4]  # ENOCONV
+    cancel = torch.ones(1, dtype=torch.int32, device=dev)
+    r = api.solve(op, f, rtol=1e-12, cancel=cancel)
+    assert r.status == [7]  # ECANCELLED
+    fbad = f.clone()
+    fbad[17, 0] = float("nan")
+    r = api.solve(op, fbad, rtol=1e-8)
+    assert r.status == [6]  # ENONFINITE
+    # the context is still usable
+    r = api.solve(op, f, rtol=1e-8)
+    assert r.status == [0]
