@@ -138,6 +138,24 @@ mvgd_status mvgd_assemble(const double *pts, int64_t n, int32_t k, const int32_t
                           int32_t *bad_rows, void *workspace, size_t workspace_bytes,
                           mvgd_stream_t stream);
 
+/* Batched assembly: many clouds (uneven sizes, any k and precision each) in
+ * ONE launch whose work items are (cloud, 32-row slice) pairs.  Each item's
+ * arrays follow the rules of mvgd_assemble; bad_rows (optional device int32)
+ * counts rows with status != 0 over the whole batch.  The workspace holds the
+ * descriptor table and the inverse orders (size from
+ * mvgd_assemble_batch_workspace_bytes with the items' point counts). */
+typedef struct {
+    const double *pts;     /* [n][3] */
+    const int32_t *nbr;    /* [n][k] from mvgd_knn */
+    mvgd_ell L;            /* n, k, prec, order and the output arrays */
+    double *h;             /* optional [n] */
+    uint8_t *row_status;   /* optional [n] */
+} mvgd_assemble_item;
+size_t mvgd_assemble_batch_workspace_bytes(const int64_t *n, int32_t count);
+mvgd_status mvgd_assemble_batch(const mvgd_assemble_item *items, int32_t count, mvgd_delta_rule rule,
+                                int32_t *bad_rows, void *workspace, size_t workspace_bytes,
+                                mvgd_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Operator application (the product every Krylov step repeats, Sec. 3.1 and
  * Sec. 4.2):  y = alpha * (sigma x - L x) + beta * y  for nrhs right-hand
@@ -175,7 +193,10 @@ typedef struct {
     int32_t inner_maxit; /* FP32_REFINE: cap per inner solve */
     double inner_rtol;   /* FP32_REFINE: inner relative tolerance, e.g. 1e-5 */
     int32_t max_outer;   /* FP32_REFINE: cap on refinement steps */
-    int32_t precond;     /* 0 = none, 1 = left diagonal (Jacobi) scaling of the Krylov system */
+    int32_t precond;     /* 0 = none; 1 = left scaling of each row of the Krylov system by
+                            1 / (|sigma| + sum_s |w_s|) (row equilibration: always positive,
+                            unlike the Jacobi divisor sigma - w_self, which can vanish on rows
+                            of irregular samples that are not diagonally dominant) */
 } mvgd_solve_opts;
 
 typedef struct {
@@ -190,6 +211,44 @@ size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t pr
 mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const double *f, double *u,
                        const mvgd_solve_opts *opts, mvgd_solve_info *info, const int32_t *cancel,
                        void *workspace, size_t workspace_bytes, mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Requests: the same solve (Sec. 4.2) split so that many systems advance in
+ * one persistent launch (uneven clouds batched together, and requests that
+ * join or leave between launches).  A request's whole solver state -- Krylov
+ * vectors, per-RHS scalars, reduction partials -- lives in its own
+ * caller-owned workspace; the operator L it was initialised with must stay
+ * alive until mvgd_request_finish.  Results of a request do not depend on
+ * which other requests share a launch: every reduction runs per request in a
+ * fixed order over fixed 512-row chunks.
+ *
+ * mvgd_request_init: gathers f (and u0, or zeros if u0 == NULL) into stored
+ *   order and sets every right-hand side to its first restart.  Asynchronous.
+ * mvgd_iterate: advances the listed requests (host array of request
+ *   workspaces, with their row and RHS counts; all of one precision) by at
+ *   most max_iterations Krylov iterations in one cooperative launch; requests
+ *   whose right-hand sides are all done cost nothing.  ctl_ws (size from
+ *   mvgd_iterate_workspace_bytes for at least this many requests and rows)
+ *   holds the launch's tables and barrier.  Asynchronous; a set cancel word
+ *   stops the launch after the current iteration.
+ * mvgd_request_finish: writes u (FP64 [n][nrhs], point order) and info
+ *   (DEVICE [nrhs]); a right-hand side not yet done reports MVGD_ENOCONV,
+ *   or MVGD_ECANCELLED / MVGD_ETIMEOUT if a launch was cut short.
+ * ------------------------------------------------------------------------ */
+size_t mvgd_request_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec);
+mvgd_status mvgd_request_init(void *req_workspace, size_t req_bytes, const mvgd_ell *L, int32_t nrhs,
+                              double sigma, const double *f, const double *u0, const mvgd_solve_opts *opts,
+                              mvgd_stream_t stream);
+size_t mvgd_iterate_workspace_bytes(int32_t max_requests, int64_t max_total_rows);
+mvgd_status mvgd_iterate(void *const *reqs, const int64_t *req_rows, const int32_t *req_nrhs, int32_t count,
+                         int32_t prec, int32_t max_iterations, const int32_t *cancel, void *ctl_workspace,
+                         size_t ctl_bytes, mvgd_stream_t stream);
+mvgd_status mvgd_request_finish(void *req_workspace, int64_t n, int32_t nrhs, double *u,
+                                mvgd_solve_info *info, mvgd_stream_t stream);
+/* done (out, DEVICE int32 [count]): 1 where every right-hand side of the
+ * request has finished (converged or stopped with a status), else 0.  A cheap
+ * check between mvgd_iterate launches.  Asynchronous. */
+mvgd_status mvgd_request_poll(void *const *reqs, int32_t count, int32_t *done, mvgd_stream_t stream);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,8 @@ SPMV_F64, SPMV_F32, SPMV_F64_HILO = 0, 1, 2
 EXPORTS = (
     "mvgd_status_string", "mvgd_version", "mvgd_knn_workspace_bytes", "mvgd_knn", "mvgd_ell_bytes",
     "mvgd_assemble_workspace_bytes", "mvgd_assemble", "mvgd_spmv", "mvgd_solve_workspace_bytes", "mvgd_solve",
+    "mvgd_request_workspace_bytes", "mvgd_request_init", "mvgd_iterate_workspace_bytes", "mvgd_iterate",
+    "mvgd_request_finish", "mvgd_assemble_batch_workspace_bytes", "mvgd_assemble_batch", "mvgd_request_poll",
 )
 
 
@@ -42,6 +44,10 @@ class SolveOpts(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("relres", C.c_double), ("status", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class AssembleItem(C.Structure):
+    _fields_ = [("pts", _P), ("nbr", _P), ("L", Ell), ("h", _P), ("row_status", _P)]
 
 
 class MvgdError(RuntimeError):
@@ -78,6 +84,24 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_solve.argtypes = [C.POINTER(Ell), C.c_int32, C.c_double, _P, _P, C.POINTER(SolveOpts), _P, _P, _P,
                              C.c_size_t, _P]
     L.mvgd_solve.restype = C.c_int
+    L.mvgd_request_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32]
+    L.mvgd_request_workspace_bytes.restype = C.c_size_t
+    L.mvgd_request_init.argtypes = [_P, C.c_size_t, C.POINTER(Ell), C.c_int32, C.c_double, _P, _P,
+                                    C.POINTER(SolveOpts), _P]
+    L.mvgd_request_init.restype = C.c_int
+    L.mvgd_iterate_workspace_bytes.argtypes = [C.c_int32, C.c_int64]
+    L.mvgd_iterate_workspace_bytes.restype = C.c_size_t
+    L.mvgd_iterate.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int32,
+                               C.c_int32, C.c_int32, _P, _P, C.c_size_t, _P]
+    L.mvgd_iterate.restype = C.c_int
+    L.mvgd_request_finish.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, _P]
+    L.mvgd_request_finish.restype = C.c_int
+    L.mvgd_assemble_batch_workspace_bytes.argtypes = [C.POINTER(C.c_int64), C.c_int32]
+    L.mvgd_assemble_batch_workspace_bytes.restype = C.c_size_t
+    L.mvgd_assemble_batch.argtypes = [C.POINTER(AssembleItem), C.c_int32, DeltaRule, _P, _P, C.c_size_t, _P]
+    L.mvgd_assemble_batch.restype = C.c_int
+    L.mvgd_request_poll.argtypes = [C.POINTER(C.c_void_p), C.c_int32, _P, _P]
+    L.mvgd_request_poll.restype = C.c_int
     _lib = L
     return L
 

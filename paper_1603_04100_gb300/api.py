@@ -168,7 +168,7 @@ class SolveResult:
 
 
 def solve(op: Operator, f: torch.Tensor, *, u0: torch.Tensor | None = None, sigma: float = 1.0,
-          rtol: float = 1e-8, maxit: int = 200000, inner_rtol: float = 1e-5, inner_maxit: int = 100000,
+          rtol: float = 1e-8, maxit: int = 200000, inner_rtol: float = 1e-5, inner_maxit: int = 20000,
           max_outer: int = 60, precond: int = 0, cancel: torch.Tensor | None = None, stream=None,
           workspace: torch.Tensor | None = None, sync: bool = True) -> SolveResult:
     """Solve (sigma I - L) u = f; f, u FP64 [n] or [n][nrhs] in point order."""

@@ -90,10 +90,11 @@ __device__ void jacobi3(double a[3][3], double v[3][3], double w[3]) {
     w[2] = a[2][2];
 }
 
-__global__ void __launch_bounds__(32) k_assemble(AsmArgs A) {
+// One 32-row slice of one cloud's operator (one warp, one row per lane).
+__device__ __forceinline__ void assemble_slice(const AsmArgs& A, int64_t slice) {
     extern __shared__ double sm[];
     const int lane = threadIdx.x;
-    const int64_t row = (int64_t)blockIdx.x * kSlice + lane;
+    const int64_t row = slice * kSlice + lane;
     const int k = A.k, m = k + 1;
     // element (r, c) of this lane's design matrix
 #define VM(r, c) sm[((r) * kCols + (c)) * kWarp + lane]
@@ -268,6 +269,39 @@ __global__ void __launch_bounds__(32) k_assemble(AsmArgs A) {
 #undef VM
 }
 
+__global__ void __launch_bounds__(32) k_assemble(AsmArgs A) { assemble_slice(A, blockIdx.x); }
+
+// Batched: many uneven clouds in one launch.  The work items are
+// (cloud, slice) pairs; block b takes the cloud whose slice range holds b.
+struct AsmItem {
+    AsmArgs a;
+    int64_t slice0;  // first global slice of this cloud
+};
+
+__global__ void __launch_bounds__(32) k_assemble_batch(const AsmItem* __restrict__ items, int count) {
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {  // last item with slice0 <= b
+        const int mid = (lo + hi + 1) >> 1;
+        if (items[mid].slice0 <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const AsmArgs A = items[lo].a;
+    assemble_slice(A, b - items[lo].slice0);
+}
+
+constexpr int kAsmGroup = 48;
+struct AsmGroup {
+    AsmItem item[kAsmGroup];
+    int count;
+};
+
+// Copies a group of descriptors (kernel parameters, so the batch is
+// capturable in a graph) into the device table.
+__global__ void k_put_items(AsmGroup G, AsmItem* dst) {
+    for (int i = threadIdx.x; i < G.count; i += blockDim.x) dst[i] = G.item[i];
+}
+
 __global__ void k_invert_order(const int32_t* __restrict__ order, int64_t n, int32_t* __restrict__ inv) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
         inv[order[r]] = (int32_t)r;
@@ -329,5 +363,84 @@ MVGD_API mvgd_status mvgd_assemble(const double* pts, int64_t n, int32_t k, cons
     MVGD_CUDA_TRY(cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int64_t nslices = n_padded(n) / kSlice;
     k_assemble<<<(unsigned)nslices, kWarp, smem, s>>>(A);
+    return launch_status();
+}
+
+MVGD_API size_t mvgd_assemble_batch_workspace_bytes(const int64_t* n, int32_t count) {
+    if (!n || count < 1) return 0;
+    size_t b = align_up(sizeof(AsmItem) * (size_t)count);
+    for (int i = 0; i < count; i++) b += n[i] > 0 ? align_up(sizeof(int32_t) * (size_t)n[i]) : 0;
+    return b;
+}
+
+MVGD_API mvgd_status mvgd_assemble_batch(const mvgd_assemble_item* items, int32_t count, mvgd_delta_rule rule,
+                                         int32_t* bad_rows, void* ws, size_t ws_bytes, mvgd_stream_t stream) {
+    if (!items || count < 1 || !ws || !aligned(ws) || !aligned(bad_rows)) return MVGD_EINVAL;
+    if (rule.kind != MVGD_DELTA_QUARTER_RANGE && rule.kind != MVGD_DELTA_MEAN_NN) return MVGD_EINVAL;
+    if (!(rule.scale > 0)) return MVGD_EINVAL;
+    size_t need = align_up(sizeof(AsmItem) * (size_t)count);
+    int kmax = 0;
+    for (int i = 0; i < count; i++) {
+        const mvgd_assemble_item& it = items[i];
+        const mvgd_ell& L = it.L;
+        const int64_t n = L.n;
+        const int k = L.k;
+        if (!it.pts || !it.nbr || n < 2 || n >= (1ll << 31) || k < kMinK || k > kMaxK || k >= n) return MVGD_EINVAL;
+        if (!L.col || !L.val || (L.prec != MVGD_FP64 && L.prec != MVGD_FP32_REFINE)) return MVGD_EINVAL;
+        if (L.prec == MVGD_FP32_REFINE && !L.val_lo) return MVGD_EINVAL;
+        if (rule.kind == MVGD_DELTA_MEAN_NN && (rule.m < 1 || rule.m > k)) return MVGD_EINVAL;
+        if (!aligned(it.pts) || !aligned(it.nbr) || !aligned(L.col) || !aligned(L.val) || !aligned(L.val_lo) ||
+            !aligned(L.order) || !aligned(it.h) || !aligned(it.row_status))
+            return MVGD_EINVAL;
+        need += align_up(sizeof(int32_t) * (size_t)n);
+        if (k > kmax) kmax = k;
+    }
+    if (ws_bytes < need) return MVGD_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (bad_rows) MVGD_CUDA_TRY(cudaMemsetAsync(bad_rows, 0, sizeof(int32_t), s));
+    Carver cv(ws);
+    AsmItem* table = cv.take<AsmItem>(count);
+    int64_t slices = 0;
+    AsmGroup G;
+    G.count = 0;
+    int group_start = 0;
+    for (int i = 0; i < count; i++) {
+        const mvgd_assemble_item& it = items[i];
+        const mvgd_ell& L = it.L;
+        int32_t* inv = cv.take<int32_t>((size_t)L.n);
+        if (L.order) {
+            int gb = (int)((L.n + 255) / 256);
+            if (gb > 4096) gb = 4096;
+            k_invert_order<<<gb, 256, 0, s>>>(L.order, L.n, inv);
+        }
+        AsmItem& a = G.item[G.count++];
+        a.a.pts = it.pts;
+        a.a.n = L.n;
+        a.a.k = L.k;
+        a.a.nbr = it.nbr;
+        a.a.order = L.order;
+        a.a.inv = L.order ? inv : nullptr;
+        a.a.delta_kind = rule.kind;
+        a.a.delta_m = rule.kind == MVGD_DELTA_MEAN_NN ? rule.m : 0;
+        a.a.delta_scale = rule.scale;
+        a.a.prec = L.prec;
+        a.a.col = L.col;
+        a.a.val = L.val;
+        a.a.val_lo = L.val_lo;
+        a.a.h_out = it.h;
+        a.a.status = it.row_status;
+        a.a.bad_rows = bad_rows;
+        a.slice0 = slices;
+        slices += n_padded(L.n) / kSlice;
+        if (G.count == kAsmGroup || i == count - 1) {
+            k_put_items<<<1, 64, 0, s>>>(G, table + group_start);
+            group_start += G.count;
+            G.count = 0;
+        }
+    }
+    size_t smem = sizeof(double) * (size_t)(kmax + 1) * kCols * kWarp;
+    MVGD_CUDA_TRY(cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (slices >= (1ll << 31)) return MVGD_EINVAL;
+    k_assemble_batch<<<(unsigned)slices, kWarp, smem, s>>>(table, count);
     return launch_status();
 }

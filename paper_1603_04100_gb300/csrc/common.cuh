@@ -61,6 +61,55 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// Compensated FP32 accumulation (the "Dot2" scheme of Ogita, Rump & Oishi,
+// SIAM J. Sci. Comput. 26(6), 2005): each product is split exactly into
+// p + e with one FMA (TwoProduct) and each addition into s + e (TwoSum), so
+// a dot product of FP32 vectors comes out as accurate as if accumulated in
+// twice the working precision, using FP32 instructions only.  The _rn
+// intrinsics keep the compiler from contracting the error terms away.
+// ---------------------------------------------------------------------------
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void f2_add_prod(F2& acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);  // exact: a*b = p + ep
+    float s, es;
+    two_sum(acc.hi, p, s, es);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(es, ep));
+}
+
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    float s, e;
+    two_sum(x.hi, y.hi, s, e);
+    F2 r;
+    r.hi = s;
+    r.lo = __fadd_rn(__fadd_rn(x.lo, y.lo), e);
+    return r;
+}
+
+__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        F2 w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = f2_add(v, w);
+    }
+    return v;
+}
+
+__device__ __forceinline__ double f2_to_double(F2 v) { return (double)v.hi + (double)v.lo; }
+
 __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
     return __shfl_sync(0xffffffffu, v, src);
 }

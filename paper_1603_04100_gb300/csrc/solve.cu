@@ -1,26 +1,32 @@
-// Device-resident Krylov solve of (sigma I - L) u = f (Sec. 4.2; the paper
-// solves with AMG -- here BiCGSTAB, van der Vorst 1992, left-preconditioned by
-// the diagonal when asked).
+// Device-resident Krylov solves of (sigma I - L) u = f (Sec. 4.2; the paper
+// solves with AMG -- here BiCGSTAB, van der Vorst 1992, optionally left-scaled
+// by the diagonal).
 //
-// One persistent cooperative kernel runs every iteration of every right-hand
-// side of every problem in the batch.  An iteration is three phases separated
-// by a grid barrier:
-//   A  p = r + beta (p - omega v) formed on the fly at the neighbours, v = A p
-//   B  s = r - alpha v formed on the fly,                              t = A s
-//   C  x += alpha p + omega s, r = s - omega t
-// Each phase ends in dot products.  Rows are cut into fixed chunks of kCh
-// rows; a chunk's partial sums are reduced in a fixed order and the block that
-// finishes a problem's last chunk of the phase sums that problem's chunks in
-// chunk order and advances its per-RHS state.  Results therefore do not depend
-// on the grid size or on which other problems share the launch.
+// Every system being solved is a "request" whose whole solver state (Krylov
+// vectors, per-RHS scalars, reduction partials) lives in its own caller-owned
+// workspace.  One persistent cooperative kernel advances any set of requests
+// together; an iteration is a fixed sequence of phases separated by a bounded
+// grid barrier:
+//   PRE_A  FP64: p = r + beta (p - omega v)       | FP32: fold u += s x on restart
+//   A      v = A p  (FP32: p formed on the fly at the neighbours)      -> (rh, v)
+//   PRE_B  FP64: s = r - alpha v                   | FP32: skipped
+//   B      t = A s  (FP32: s formed on the fly)                     -> (t, s), (t, t)
+//   C      x += alpha p + omega s, r = s - omega t                  -> (rh, r), (r, r)
+// FP64 materialises p and s because forming them at every neighbour would
+// multiply the FP64 work by K on a part whose FP64 pipe is 1/56 of FP32; the
+// FP32 path forms them on the fly and saves two barriers.  Rows are cut into
+// fixed chunks of kCh rows; a chunk's partials are reduced in a fixed order
+// and the block that finishes a request's last chunk of a phase sums that
+// request's partials in chunk order and advances its per-RHS state.  Results
+// therefore depend neither on the grid size nor on the other requests.
 //
-// Per right-hand side a small state machine runs:
-//   RESTART  FP64 true residual r64 = f - A u  (mixed: on hi + lo weights,
-//            after folding the last inner correction into u); stop if
-//            ||r64|| <= rtol ||f||; else restart the Krylov vectors from
-//            D^-1 r64 (mixed: scaled by 1 / ||r64||, in FP32)
-//   INNER    BiCGSTAB iterations (mixed: FP32 on hi weights in difference
-//            form) until the recursive residual meets the restart target
+// Per right-hand side:
+//   RESTART  FP64 true residual r64 = f - A u (FP32 path: on hi + lo weights,
+//            after folding the last inner correction into u); stop at rtol,
+//            else restart the Krylov vectors from D^-1 r64 (FP32 path: scaled
+//            by 1 / ||r64|| and rounded to FP32)
+//   INNER    BiCGSTAB until the recursive residual meets the restart target;
+//            a diverging FP32 inner solve is abandoned and its correction dropped
 //   DONE
 #include <type_traits>
 
@@ -29,30 +35,42 @@
 namespace mvgd {
 namespace {
 
-constexpr int kCh = 2048;
+constexpr int kCh = 512;
 constexpr int kThreads = 256;
 constexpr int kRowsPerThread = kCh / kThreads;
 constexpr int kChan = 2;
+constexpr int kRedSlots = 3;
+constexpr int kMaxReq = 1024;
 
+enum Phase : int { P_PRE_A = 0, P_A = 1, P_PRE_B = 2, P_B = 3, P_C = 4, P_COUNT = 5 };
 enum Mode : int { M_RESTART = 0, M_INNER = 1, M_SKIP = 2, M_DONE = 3 };
+
+__host__ __device__ constexpr int red_slot(int ph) { return ph == P_A ? 0 : (ph == P_B ? 1 : 2); }
 
 struct RhsState {
     double rho, alpha, omega, beta;
     double fnorm, relres, scale, target;
-    double rnorm, pad0;
-    int mode, pp, iters, inner_iters, outer, status;
+    double rnorm, rmin;
+    int mode, pp, iters, inner_iters, outer, status, discard, stall;
+    int best_flag;   // the last iteration reached a new smallest inner residual: copy x to x_best
+    int fold_best;   // on restart, fold x_best (not x) into u
+    int since_best;  // inner iterations since the smallest residual last dropped by 1%
+    int pad1;
 };
 
+// One request: an operator, its right-hand sides and all solver state.
 struct Prob {
     int64_t n;
-    int k, Q;
+    int k, Q, prec, precond;
     double sigma;
     const int32_t* col;
     const void* val;
     const float* val_lo;
-    const double* f;
-    double* u;
+    const int32_t* order;
+    double* f;         // stored order [n][Q]
+    double* u;         // stored order [n][Q]
     void* x;
+    void* xb;          // FP32 path: the inner iterate with the smallest residual so far
     void* r;
     void* rh;
     void* p[2];
@@ -60,87 +78,134 @@ struct Prob {
     void* s;
     void* t;
     double* r64;
-    RhsState* st;
-    double* part;      // [3][kChan][nchunk][Q]
-    unsigned* arrive;  // [3]
-    int chunk0, nchunk;
+    void* invd;        // [n] VT: 1 / (sigma + sum_s |w_s|), the left scaling (precond == 1)
+    RhsState* st;      // [Q]
+    double* part;      // [kRedSlots][kChan][nchunk][Q]
+    unsigned* arrive;  // [kRedSlots]
+    int nchunk, pad;
     double rtol, inner_rtol;
-    int maxit, inner_maxit, max_outer, precond;
+    int maxit, inner_maxit, max_outer, pad2;
 };
 
 struct Ctl {
     GridBarrier bar;
     int* err;
-    int* active;
-    const int* cancel;
+    int* active;     // right-hand sides not DONE
+    int* nrestart;   // right-hand sides in RESTART
     int* stop;
+    const int* cancel;
     long long limit;
 };
 
-template <typename T>
-__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+__device__ __forceinline__ void load_state(RhsState& dst, const RhsState* src) {
+    const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(&dst);
+#pragma unroll
+    for (int w = 0; w < (int)(sizeof(RhsState) / 8); w++) d[w] = __ldcg(s + w);
+}
 
-// Row loops --------------------------------------------------------------------
+// ------------------------------------------------------------------------------
+// Row work
+// ------------------------------------------------------------------------------
 
+// PRE_A / PRE_B / C and the RESTART steps: elementwise on row r.
 template <bool MIXED, int QT>
-__device__ __forceinline__ void inner_row(const Prob& P, int64_t r, int ph, const RhsState* S, const bool (&on)[QT],
-                                          float (&af)[kChan][QT], double (&ad)[kChan][QT]) {
+__device__ __forceinline__ void elementwise_row(const Prob& P, int64_t r, int ph, const RhsState* S,
+                                                const bool (&inner)[QT], const bool (&restart)[QT],
+                                                F2 (&af)[kChan][QT]) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
+    const int Q = P.Q;
+#pragma unroll
+    for (int q = 0; q < QT; q++) {
+        const int64_t e = r * Q + q;
+        if (ph == P_PRE_A) {
+            if (MIXED && restart[q] && S[q].outer > 0 && !S[q].discard)
+                P.u[e] += S[q].scale * (double)static_cast<const VT*>(S[q].fold_best ? P.xb : P.x)[e];
+            if (!MIXED && inner[q]) {
+                VT* pv = static_cast<VT*>(P.p[0]);
+                const VT* vv = static_cast<const VT*>(P.v[0]);
+                const VT* rv = static_cast<const VT*>(P.r);
+                pv[e] = rv[e] + (VT)S[q].beta * (pv[e] - (VT)S[q].omega * vv[e]);
+            }
+        } else if (ph == P_PRE_B) {
+            if (!MIXED && inner[q]) {
+                const VT* vv = static_cast<const VT*>(P.v[0]);
+                const VT* rv = static_cast<const VT*>(P.r);
+                static_cast<VT*>(P.s)[e] = rv[e] - (VT)S[q].alpha * vv[e];
+            }
+        } else if (ph == P_C) {
+            if (inner[q]) {
+                const VT* pv = static_cast<const VT*>(P.p[S[q].pp]);
+                VT* X = static_cast<VT*>(P.x);
+                const VT sv = static_cast<const VT*>(P.s)[e], tv = static_cast<const VT*>(P.t)[e];
+                const VT al = (VT)S[q].alpha, om = (VT)S[q].omega;
+                X[e] = X[e] + al * pv[e] + om * sv;
+                const VT rn = sv - om * tv;
+                static_cast<VT*>(P.r)[e] = rn;
+                const VT rhv = static_cast<const VT*>(P.rh)[e];
+                f2_add_prod(af[0][q], (float)rhv, (float)rn);
+                f2_add_prod(af[1][q], (float)rn, (float)rn);
+            }
+        }
+    }
+}
+
+// FP64 partials of the FP64 steps (C of the plain path) go through a double
+// accumulator so that nothing is rounded to FP32.
+template <int QT>
+__device__ __forceinline__ void c_row_f64(const Prob& P, int64_t r, const RhsState* S, const bool (&inner)[QT],
+                                          double (&ad)[kChan][QT]) {
+    const int Q = P.Q;
+#pragma unroll
+    for (int q = 0; q < QT; q++) {
+        if (!inner[q]) continue;
+        const int64_t e = r * Q + q;
+        const double* pv = static_cast<const double*>(P.p[0]);
+        double* X = static_cast<double*>(P.x);
+        const double sv = static_cast<const double*>(P.s)[e], tv = static_cast<const double*>(P.t)[e];
+        X[e] = X[e] + S[q].alpha * pv[e] + S[q].omega * sv;
+        const double rn = sv - S[q].omega * tv;
+        static_cast<double*>(P.r)[e] = rn;
+        ad[0][q] += static_cast<const double*>(P.rh)[e] * rn;
+        ad[1][q] += rn * rn;
+    }
+}
+
+// A / B for INNER right-hand sides: one operator application each.
+template <bool MIXED, int QT>
+__device__ __forceinline__ void spmv_row(const Prob& P, int64_t r, int ph, const RhsState* S, const bool (&on)[QT],
+                                         const float (&c1)[QT], const float (&c2)[QT], F2 (&af)[kChan][QT],
+                                         double (&ad)[kChan][QT]) {
     using VT = typename std::conditional<MIXED, float, double>::type;
     const int Q = P.Q, k = P.k, m = k + 1;
     const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
     const int64_t cb = (r / kSlice) * (int64_t)(kSlice * k) + (r % kSlice);
     const VT* __restrict__ val = static_cast<const VT*>(P.val);
+    const VT sig = (VT)P.sigma;
+    const VT w0 = val[vb];
+    const VT invd = P.precond ? static_cast<const VT*>(P.invd)[r] : (VT)1;
     // vectors written by other blocks during this kernel: plain (coherent) loads
     const VT* R = static_cast<const VT*>(P.r);
     const VT* RH = static_cast<const VT*>(P.rh);
-    const VT sig = (VT)P.sigma;
-    const VT w0 = val[vb];
-    const VT invd = P.precond ? (VT)1 / (sig - w0) : (VT)1;
-
-    if (ph == 2) {
-#pragma unroll
-        for (int q = 0; q < QT; q++) {
-            if (!on[q]) continue;
-            const int64_t e = r * Q + q;
-            const VT* pv = static_cast<const VT*>(P.p[S[q].pp]);
-            VT* X = static_cast<VT*>(P.x);
-            const VT sv = static_cast<const VT*>(P.s)[e], tv = static_cast<const VT*>(P.t)[e];
-            const VT al = (VT)S[q].alpha, om = (VT)S[q].omega;
-            X[e] = X[e] + al * pv[e] + om * sv;
-            const VT rn = sv - om * tv;
-            static_cast<VT*>(P.r)[e] = rn;
-            if (MIXED) {
-                af[0][q] += (float)(RH[e] * rn);
-                af[1][q] += (float)(rn * rn);
-            } else {
-                ad[0][q] += (double)(RH[e] * rn);
-                ad[1][q] += (double)(rn * rn);
-            }
-        }
-        return;
-    }
-    // phases A and B: one operator application per active right-hand side
-    VT si[QT], acc[QT];
-    const VT* pold[QT];
+    const VT* src[QT];
     const VT* vold[QT];
-    VT c1[QT], c2[QT];
+    VT si[QT], acc[QT];
 #pragma unroll
     for (int q = 0; q < QT; q++) {
         acc[q] = (VT)0;
         si[q] = (VT)0;
+        src[q] = nullptr;
+        vold[q] = nullptr;
         if (!on[q]) continue;
-        const int pp = S[q].pp;
-        vold[q] = static_cast<const VT*>(P.v[pp]);
-        pold[q] = static_cast<const VT*>(P.p[pp]);
-        if (ph == 0) {
-            c1[q] = (VT)S[q].beta;
-            c2[q] = (VT)S[q].omega;
-            const int64_t e = r * Q + q;
-            si[q] = R[e] + c1[q] * (pold[q][e] - c2[q] * vold[q][e]);
+        const int64_t e = r * Q + q;
+        if (MIXED) {
+            vold[q] = static_cast<const VT*>(P.v[S[q].pp]);
+            src[q] = static_cast<const VT*>(P.p[S[q].pp]);
+            si[q] = (ph == P_A) ? R[e] + (VT)c1[q] * (src[q][e] - (VT)c2[q] * vold[q][e])
+                                : R[e] - (VT)c1[q] * vold[q][e];
         } else {
-            c1[q] = (VT)S[q].alpha;
-            const int64_t e = r * Q + q;
-            si[q] = R[e] - c1[q] * vold[q][e];
+            src[q] = static_cast<const VT*>(ph == P_A ? P.p[0] : P.s);
+            si[q] = src[q][e];
         }
     }
 #pragma unroll 4
@@ -151,11 +216,13 @@ __device__ __forceinline__ void inner_row(const Prob& P, int64_t r, int ph, cons
         for (int q = 0; q < QT; q++) {
             if (!on[q]) continue;
             const int64_t e = j * Q + q;
-            VT sj;
-            if (ph == 0) sj = R[e] + c1[q] * (pold[q][e] - c2[q] * vold[q][e]);
-            else sj = R[e] - c1[q] * vold[q][e];
-            if (MIXED) acc[q] += w * (sj - si[q]);
-            else acc[q] += w * sj;
+            if (MIXED) {
+                const VT sj = (ph == P_A) ? R[e] + (VT)c1[q] * (src[q][e] - (VT)c2[q] * vold[q][e])
+                                          : R[e] - (VT)c1[q] * vold[q][e];
+                acc[q] = fmaf(w, sj - si[q], acc[q]);
+            } else {
+                acc[q] = fma(w, src[q][e], acc[q]);
+            }
         }
     }
 #pragma unroll
@@ -164,19 +231,20 @@ __device__ __forceinline__ void inner_row(const Prob& P, int64_t r, int ph, cons
         const int64_t e = r * Q + q;
         const VT lx = MIXED ? acc[q] : acc[q] + w0 * si[q];
         const VT res = invd * (sig * si[q] - lx);
-        if (ph == 0) {
-            // new p and v go to the other ping-pong buffers
-            const int np = S[q].pp ^ 1;
-            static_cast<VT*>(P.p[np])[e] = si[q];
+        if (ph == P_A) {
+            const int np = MIXED ? (S[q].pp ^ 1) : 0;
+            if (MIXED) static_cast<VT*>(P.p[np])[e] = si[q];
+            // the previous iteration reached a new best residual: keep its iterate
+            if (MIXED && S[q].best_flag) static_cast<VT*>(P.xb)[e] = static_cast<const VT*>(P.x)[e];
             static_cast<VT*>(P.v[np])[e] = res;
-            if (MIXED) af[0][q] += (float)(RH[e] * res);
+            if (MIXED) f2_add_prod(af[0][q], (float)RH[e], (float)res);
             else ad[0][q] += (double)(RH[e] * res);
         } else {
-            static_cast<VT*>(P.s)[e] = si[q];
+            if (MIXED) static_cast<VT*>(P.s)[e] = si[q];
             static_cast<VT*>(P.t)[e] = res;
             if (MIXED) {
-                af[0][q] += (float)(res * si[q]);
-                af[1][q] += (float)(res * res);
+                f2_add_prod(af[0][q], (float)res, (float)si[q]);
+                f2_add_prod(af[1][q], (float)res, (float)res);
             } else {
                 ad[0][q] += (double)(res * si[q]);
                 ad[1][q] += (double)(res * res);
@@ -185,6 +253,7 @@ __device__ __forceinline__ void inner_row(const Prob& P, int64_t r, int ph, cons
     }
 }
 
+// RESTART steps A (FP64 true residual) and B (restart the Krylov vectors).
 template <bool MIXED, int QT>
 __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, const RhsState* S, const bool (&on)[QT],
                                             double (&ad)[kChan][QT]) {
@@ -192,18 +261,7 @@ __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, co
     const int Q = P.Q, k = P.k, m = k + 1;
     const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
     const int64_t cb = (r / kSlice) * (int64_t)(kSlice * k) + (r % kSlice);
-    if (ph == 0) {
-        if (!MIXED) return;
-#pragma unroll
-        for (int q = 0; q < QT; q++) {
-            if (!on[q] || S[q].outer == 0) continue;
-            const int64_t e = r * Q + q;
-            P.u[e] += S[q].scale * (double)static_cast<const VT*>(P.x)[e];
-        }
-        return;
-    }
-    if (ph == 1) {
-        // true residual in FP64
+    if (ph == P_A) {
         double w0;
         if (MIXED) w0 = (double)static_cast<const float*>(P.val)[vb] + (double)P.val_lo[vb];
         else w0 = static_cast<const double*>(P.val)[vb];
@@ -236,12 +294,8 @@ __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, co
         }
         return;
     }
-    // ph == 2: restart the Krylov vectors from D^-1 r64 (scaled in the mixed path)
-    double invd = 1.0;
-    if (P.precond) {
-        double w0 = MIXED ? (double)static_cast<const float*>(P.val)[vb] : static_cast<const double*>(P.val)[vb];
-        invd = 1.0 / (P.sigma - w0);
-    }
+    // ph == P_C: restart the Krylov vectors
+    const double invd = P.precond ? (double)static_cast<const VT*>(P.invd)[r] : 1.0;
 #pragma unroll
     for (int q = 0; q < QT; q++) {
         if (!on[q]) continue;
@@ -250,37 +304,71 @@ __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, co
         if (MIXED) rv /= S[q].scale;
         const VT rr = (VT)rv;
         static_cast<VT*>(P.r)[e] = rr;
-        static_cast<VT*>(P.rh)[e] = rr;
+        // shadow residual: r itself; after a refinement step that did not lower the
+        // residual, a deterministic relative perturbation of up to +-50% sends the
+        // retry down a different Krylov path ((rh, r) stays positive)
+        VT rhv = rr;
+        if (S[q].stall > 0) {
+            uint32_t hsh = (uint32_t)e * 2654435761u ^ (uint32_t)S[q].outer * 40503u;
+            hsh ^= hsh >> 16; hsh *= 0x7feb352du; hsh ^= hsh >> 15; hsh *= 0x846ca68bu; hsh ^= hsh >> 16;
+            const double u01 = (double)hsh * (1.0 / 4294967296.0);
+            rhv = (VT)(rv * (1.0 + (u01 - 0.5)));
+        }
+        static_cast<VT*>(P.rh)[e] = rhv;
         static_cast<VT*>(P.p[0])[e] = (VT)0;
-        static_cast<VT*>(P.p[1])[e] = (VT)0;
         static_cast<VT*>(P.v[0])[e] = (VT)0;
-        static_cast<VT*>(P.v[1])[e] = (VT)0;
-        if (MIXED) static_cast<VT*>(P.x)[e] = (VT)0;
+        if (MIXED) {
+            static_cast<VT*>(P.p[1])[e] = (VT)0;
+            static_cast<VT*>(P.v[1])[e] = (VT)0;
+            static_cast<VT*>(P.x)[e] = (VT)0;
+            static_cast<VT*>(P.xb)[e] = (VT)0;
+        }
         ad[0][q] += (double)rr * (double)rr;
     }
 }
 
-// State transitions -------------------------------------------------------------
-
+// ------------------------------------------------------------------------------
+// State transitions (run by the block that finishes a request's phase)
+// ------------------------------------------------------------------------------
 template <bool MIXED>
-__device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, int* active) {
+__device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, const Ctl& ctl) {
     switch (T.mode) {
         case M_INNER:
-            if (ph == 0) {
-                T.pp ^= 1;
+            if (ph == P_A) {
+                if (MIXED) T.pp ^= 1;
                 if (!(fabs(a) > 0.0) || !isfinite(a)) T.mode = M_SKIP;
                 else T.alpha = T.rho / a;
-            } else if (ph == 1) {
+            } else if (ph == P_B) {
                 T.omega = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
-            } else {
+            } else if (ph == P_C) {
                 T.iters++;
                 T.inner_iters++;
                 const double rn = sqrt(b);
                 T.rnorm = rn;
-                bool restart = !isfinite(rn) || !isfinite(a) || rn <= T.target || T.iters >= P.maxit ||
+                const bool finite = isfinite(rn) && isfinite(a);
+                // FP32 path: remember the iterate with the smallest residual; an
+                // inner solve that stagnates or starts to diverge ends there and
+                // hands back that best iterate instead of its last one
+                const bool improved = finite && rn < T.rmin;
+                if (improved) {
+                    T.since_best = (rn < 0.99 * T.rmin) ? 0 : T.since_best + 1;
+                    T.rmin = rn;
+                } else {
+                    T.since_best++;
+                }
+                T.best_flag = improved ? 1 : 0;
+                const bool diverging = MIXED && finite && rn > 1e4 * T.rmin;
+                const bool stagnating = MIXED && T.since_best > 200 && 2 * T.since_best > T.inner_iters;
+                bool restart = !finite || diverging || stagnating || rn <= T.target || T.iters >= P.maxit ||
                                T.omega == 0.0 || a == 0.0 || (MIXED && T.inner_iters >= P.inner_maxit);
                 if (restart) {
+                    // x_best only ever holds finite iterates with smaller residuals (or
+                    // the zero start), so folding it is always safe
+                    T.discard = 0;
+                    T.fold_best = improved ? 0 : 1;  // the current iterate is the best one iff it just improved
+                    T.best_flag = 0;
                     T.mode = M_RESTART;
+                    atomicAdd(ctl.nrestart, 1);
                 } else {
                     T.beta = (a / T.rho) * (T.alpha / T.omega);
                     T.rho = a;
@@ -288,45 +376,62 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
             }
             break;
         case M_SKIP:
-            if (ph == 2) T.mode = M_RESTART;
+            if (ph == P_C) {
+                T.mode = M_RESTART;
+                T.discard = 0;
+                atomicAdd(ctl.nrestart, 1);
+            }
             break;
         case M_RESTART:
-            if (ph == 1) {
+            if (ph == P_A) {
                 if (T.fnorm < 0) {
                     const double fn = sqrt(b);
                     T.fnorm = fn > 0 ? fn : 1.0;
                 }
                 const double rn = sqrt(a);
-                T.relres = rn / T.fnorm;
+                const double rel = rn / T.fnorm;
+                if (T.outer > 0 && !(rel < T.relres)) T.stall++;
+                else T.stall = 0;
+                T.relres = rel;
                 if (!isfinite(rn)) {
                     T.mode = M_DONE;
                     T.status = MVGD_ENONFINITE;
-                } else if (T.relres <= P.rtol) {
+                } else if (rel <= P.rtol) {
                     T.mode = M_DONE;
                     T.status = MVGD_OK;
                 } else if (T.iters >= P.maxit) {
                     T.mode = M_DONE;
                     T.status = MVGD_ENOCONV;
-                } else if (T.outer >= P.max_outer) {
+                } else if (T.outer >= P.max_outer || T.stall >= 4) {
                     T.mode = M_DONE;
                     T.status = MVGD_EBREAKDOWN;
                 } else {
                     T.scale = rn;
                 }
-                if (T.mode == M_DONE) atomicSub(active, 1);
-            } else if (ph == 2) {
+                if (T.mode == M_DONE) {
+                    atomicSub(ctl.active, 1);
+                    atomicSub(ctl.nrestart, 1);
+                }
+            } else if (ph == P_C) {
                 const double rn = sqrt(a);
                 T.rho = a;
                 T.alpha = 1.0;
                 T.omega = 1.0;
                 T.beta = 0.0;
                 T.pp = 0;
+                T.rmin = rn;
+                T.rnorm = rn;
                 double red = 0.5 * P.rtol / T.relres;
                 if (MIXED) red = fmax(P.inner_rtol, red);
                 T.target = red * rn;
                 T.outer++;
                 T.inner_iters = 0;
+                T.discard = 0;
+                T.best_flag = 0;
+                T.fold_best = 0;
+                T.since_best = 0;
                 T.mode = M_INNER;
+                atomicSub(ctl.nrestart, 1);
             }
             break;
         default:
@@ -334,10 +439,14 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
     }
 }
 
+struct ReqTable {
+    const Prob* const* prob;  // [count]
+    const int* chunk_req;     // [nchunks]
+    const int* chunk_base;    // [count] first chunk of each request
+};
+
 template <bool MIXED, int QT>
-__global__ void __launch_bounds__(kThreads) k_solve(const Prob* __restrict__ probs,
-                                                     const int* __restrict__ chunk_prob, int nchunks, Ctl ctl,
-                                                     int iter_budget) {
+__global__ void __launch_bounds__(kThreads) k_solve(ReqTable tab, int nchunks, Ctl ctl, int iter_budget) {
     __shared__ RhsState S[QT];
     __shared__ double red[kThreads / 32][kChan * QT];
     __shared__ double tot[kChan * QT];
@@ -345,60 +454,91 @@ __global__ void __launch_bounds__(kThreads) k_solve(const Prob* __restrict__ pro
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
     for (int it = 0; it < iter_budget; ++it) {
-        for (int ph = 0; ph < 3; ++ph) {
+        // read after the last barrier of the previous iteration: identical in every block
+        const bool pre_a = !MIXED || *(volatile int*)ctl.nrestart > 0;
+        for (int ph = 0; ph < P_COUNT; ++ph) {
+            if (ph == P_PRE_A && !pre_a) continue;
+            if (ph == P_PRE_B && MIXED) continue;
+            const bool reduce = ph == P_A || ph == P_B || ph == P_C;
             for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-                const Prob& P = probs[chunk_prob[c]];
-                const int lc = c - P.chunk0;
+                const int ri = tab.chunk_req[c];
+                const Prob& P = *tab.prob[ri];
+                const int lc = c - tab.chunk_base[ri];
                 if (tid < QT) {
-                    if (tid < P.Q) S[tid] = P.st[tid];
+                    if (tid < P.Q) load_state(S[tid], P.st + tid);
                     else S[tid].mode = M_DONE;
                 }
                 __syncthreads();
-                bool on_inner[QT], on_restart[QT];
-                bool any_inner = false, any_restart = false;
+                bool inner[QT], restart[QT];
+                bool any_inner = false, any_restart = false, all_done = true;
+                float c1[QT], c2[QT];
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
-                    on_inner[q] = S[q].mode == M_INNER;
-                    on_restart[q] = S[q].mode == M_RESTART;
-                    any_inner |= on_inner[q];
-                    any_restart |= on_restart[q];
+                    const int md = S[q].mode;
+                    inner[q] = md == M_INNER;
+                    restart[q] = md == M_RESTART;
+                    any_inner |= inner[q];
+                    any_restart |= restart[q];
+                    all_done &= (md == M_DONE);
+                    c1[q] = (float)(ph == P_A ? S[q].beta : S[q].alpha);
+                    c2[q] = (float)S[q].omega;
                 }
-                float af[kChan][QT];
+                if (all_done) {  // the whole request is finished: no work, no arrival
+                    __syncthreads();
+                    continue;
+                }
+                F2 af[kChan][QT];
                 double ad[kChan][QT];
 #pragma unroll
                 for (int ch = 0; ch < kChan; ch++)
 #pragma unroll
-                    for (int q = 0; q < QT; q++) { af[ch][q] = 0.0f; ad[ch][q] = 0.0; }
+                    for (int q = 0; q < QT; q++) { af[ch][q].hi = 0.0f; af[ch][q].lo = 0.0f; ad[ch][q] = 0.0; }
                 const int64_t row0 = (int64_t)lc * kCh;
                 for (int j = 0; j < kRowsPerThread; ++j) {
                     const int64_t r = row0 + (int64_t)j * kThreads + tid;
                     if (r >= P.n) break;
-                    if (any_inner) inner_row<MIXED, QT>(P, r, ph, S, on_inner, af, ad);
-                    if (any_restart) restart_row<MIXED, QT>(P, r, ph, S, on_restart, ad);
+                    // a restart computes its residual in A and resets the Krylov vectors in C,
+                    // so that its first inner step starts at the next iteration's A
+                    if (ph == P_A || ph == P_B) {
+                        if (any_inner) spmv_row<MIXED, QT>(P, r, ph, S, inner, c1, c2, af, ad);
+                        if (any_restart && ph == P_A) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
+                    } else if (ph == P_C) {
+                        if (any_inner) {
+                            if (MIXED) elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
+                            else c_row_f64<QT>(P, r, S, inner, ad);
+                        }
+                        if (any_restart) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
+                    } else {
+                        elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
+                    }
                 }
-                // block reduction in a fixed order
+                if (!reduce) {
+                    __syncthreads();
+                    continue;
+                }
+                // block reduction in a fixed order: FP32 partials within the warp in FP32
 #pragma unroll
                 for (int ch = 0; ch < kChan; ch++)
 #pragma unroll
                     for (int q = 0; q < QT; q++) {
-                        double v = ad[ch][q] + (double)af[ch][q];
-                        v = warp_sum(v);
+                        double v = f2_to_double(warp_sum_f2(af[ch][q]));
+                        if (any_restart || !MIXED) v += warp_sum(ad[ch][q]);
                         if (lane == 0) red[wid][ch * QT + q] = v;
                     }
                 __syncthreads();
+                const int slot = red_slot(ph);
                 if (tid < kChan * QT) {
                     double v = 0.0;
                     for (int w = 0; w < kThreads / 32; w++) v += red[w][tid];
                     const int ch = tid / QT, q = tid % QT;
-                    if (q < P.Q) P.part[(((int64_t)ph * kChan + ch) * P.nchunk + lc) * P.Q + q] = v;
+                    if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + lc) * P.Q + q] = v;
                 }
                 __threadfence();
                 __syncthreads();
-                if (tid == 0) last = (atomicAdd(&P.arrive[ph], 1u) == (unsigned)(P.nchunk - 1));
+                if (tid == 0) last = (atomicAdd(&P.arrive[slot], 1u) == (unsigned)(P.nchunk - 1));
                 __syncthreads();
                 if (last) {
                     __threadfence();
-                    // sum this problem's chunk partials in chunk order
                     double acc[kChan * QT];
 #pragma unroll
                     for (int e = 0; e < kChan * QT; e++) acc[e] = 0.0;
@@ -406,7 +546,8 @@ __global__ void __launch_bounds__(kThreads) k_solve(const Prob* __restrict__ pro
 #pragma unroll
                         for (int e = 0; e < kChan * QT; e++) {
                             const int ch = e / QT, q = e % QT;
-                            if (q < P.Q) acc[e] += ldcg(&P.part[(((int64_t)ph * kChan + ch) * P.nchunk + l) * P.Q + q]);
+                            if (q < P.Q)
+                                acc[e] += __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q]);
                         }
 #pragma unroll
                     for (int e = 0; e < kChan * QT; e++) {
@@ -422,17 +563,17 @@ __global__ void __launch_bounds__(kThreads) k_solve(const Prob* __restrict__ pro
                     __syncthreads();
                     if (tid < P.Q) {
                         RhsState T = S[tid];
-                        advance<MIXED>(P, ph, T, tot[0 * QT + tid], tot[1 * QT + tid], ctl.active);
+                        advance<MIXED>(P, ph, T, tot[0 * QT + tid], tot[1 * QT + tid], ctl);
                         P.st[tid] = T;
                     }
-                    if (tid == 0) P.arrive[ph] = 0;
+                    if (tid == 0) P.arrive[slot] = 0;
                     __threadfence();
                 }
                 __syncthreads();
             }
-            // the stop word is written only before the last barrier of an iteration and read
-            // only after it, so every block takes the same exit decision
-            if (ph == 2 && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
+            // the stop word is written only before the last barrier of an iteration and
+            // read only after it, so every block takes the same exit decision
+            if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
                 *ctl.stop = 1;
             if (!grid_sync(ctl.bar, ctl.err, ctl.limit)) return;
         }
@@ -440,11 +581,67 @@ __global__ void __launch_bounds__(kThreads) k_solve(const Prob* __restrict__ pro
     }
 }
 
-// Setup / teardown kernels --------------------------------------------------------
+// ------------------------------------------------------------------------------
+// Request workspace layout, set-up and tear-down
+// ------------------------------------------------------------------------------
+struct ReqLayout {
+    Prob* prob;
+    RhsState* st;
+    double* part;
+    unsigned* arrive;
+    mvgd_solve_info* info;
+    double* fs;
+    double* us;
+    double* r64;
+    void* invd;
+    void* vec[10];  // x r rh p0 p1 v0 v1 s t x_best
+    size_t bytes;
+};
 
-__global__ void k_init_states(RhsState* st, int Q, unsigned* arrive, unsigned* bar, int* ctl_words, int active) {
-    int t = threadIdx.x;
-    if (t < Q) {
+ReqLayout req_layout(void* ws, int64_t n, int Q, int prec) {
+    ReqLayout L;
+    Carver cv(ws);
+    const int64_t nchunk = (n + kCh - 1) / kCh;
+    const size_t vt = prec == MVGD_FP64 ? sizeof(double) : sizeof(float);
+    L.prob = cv.take<Prob>(1);
+    L.st = cv.take<RhsState>(Q);
+    L.part = cv.take<double>(kRedSlots * kChan * nchunk * Q);
+    L.arrive = cv.take<unsigned>(kRedSlots);
+    L.info = cv.take<mvgd_solve_info>(Q);
+    L.fs = cv.take<double>(n * Q);
+    L.us = cv.take<double>(n * Q);
+    L.r64 = cv.take<double>(n * Q);
+    L.invd = cv.take<char>(vt * n);
+    for (int v = 0; v < 10; v++) L.vec[v] = cv.take<char>(vt * n * Q);
+    L.bytes = cv.used;
+    return L;
+}
+
+struct CtlLayout {
+    unsigned* bar;
+    int* words;     // err, active, nrestart, stop
+    const Prob** prob;
+    int* chunk_req;
+    int* chunk_base;
+    size_t bytes;
+};
+
+CtlLayout ctl_layout(void* ws, int max_req, int64_t max_chunks) {
+    CtlLayout C;
+    Carver cv(ws);
+    C.bar = cv.take<unsigned>(2);
+    C.words = cv.take<int>(4);
+    C.prob = cv.take<const Prob*>(max_req);
+    C.chunk_req = cv.take<int>(max_chunks);
+    C.chunk_base = cv.take<int>(max_req);
+    C.bytes = cv.used;
+    return C;
+}
+
+__global__ void k_request_init(Prob P, Prob* dst, int64_t n) {
+    // Prob travels by value (kernel parameter), so set-up is capturable in a graph
+    if (blockIdx.x == 0 && threadIdx.x == 0) *dst = P;
+    if (blockIdx.x == 0 && threadIdx.x < P.Q) {
         RhsState T;
         T.rho = T.alpha = T.omega = 1.0;
         T.beta = 0.0;
@@ -453,93 +650,154 @@ __global__ void k_init_states(RhsState* st, int Q, unsigned* arrive, unsigned* b
         T.scale = 0.0;
         T.target = 0.0;
         T.rnorm = 0.0;
-        T.pad0 = 0.0;
+        T.rmin = 0.0;
         T.mode = M_RESTART;
         T.pp = 0;
         T.iters = T.inner_iters = T.outer = 0;
         T.status = MVGD_OK;
-        st[t] = T;
+        T.discard = 0;
+        T.stall = 0;
+        T.best_flag = T.fold_best = T.since_best = T.pad1 = 0;
+        P.st[threadIdx.x] = T;
     }
-    if (t < 3) arrive[t] = 0;
-    if (t < 2) bar[t] = 0;
-    if (t == 0) {
-        ctl_words[0] = 0;       // err
-        ctl_words[1] = active;  // active
-        ctl_words[2] = 0;       // stop
+    if (blockIdx.x == 0 && threadIdx.x < kRedSlots) P.arrive[threadIdx.x] = 0;
+}
+
+// Left scaling of the Krylov system: d_r = sigma + sum_s |w_rs| over the row's
+// FP64 (or hi + lo) weights.  Always positive, unlike sigma - w_self: rows of an
+// MVGD operator on irregular samples need not be diagonally dominant, and a
+// self weight near sigma would make the Jacobi divisor vanish.
+__global__ void k_prep_scaling(Prob P) {
+    const int k = P.k, m = k + 1;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
+        double d = fabs(P.sigma);
+        for (int s = 0; s < m; s++) {
+            const int64_t e = vb + (int64_t)s * kSlice;
+            double w = P.prec == MVGD_FP64 ? static_cast<const double*>(P.val)[e]
+                                           : (double)static_cast<const float*>(P.val)[e] + (double)P.val_lo[e];
+            d += fabs(w);
+        }
+        const double inv = d > 0 ? 1.0 / d : 1.0;
+        if (P.prec == MVGD_FP64) static_cast<double*>(P.invd)[r] = inv;
+        else static_cast<float*>(P.invd)[r] = (float)inv;
     }
 }
 
-__global__ void k_finish(const RhsState* st, int Q, const int* ctl_words, mvgd_solve_info* out) {
-    int q = threadIdx.x;
-    if (q >= Q) return;
-    RhsState T = st[q];
+__global__ void k_gather_rows(const double* __restrict__ src, const int32_t* __restrict__ order, int64_t n, int Q,
+                              double* __restrict__ dst, int zero) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * Q; e += (int64_t)gridDim.x * blockDim.x) {
+        if (zero || src == nullptr) { dst[e] = 0.0; continue; }
+        const int64_t r = e / Q, q = e % Q;
+        const int64_t from = order ? (int64_t)order[r] : r;
+        dst[e] = src[from * Q + q];
+    }
+}
+
+__global__ void k_finish(const Prob* P, mvgd_solve_info* out) {
+    const int q = threadIdx.x;
+    if (q >= P->Q) return;
+    RhsState T;
+    load_state(T, P->st + q);
     mvgd_solve_info I;
     I.iters = T.iters;
     I.outer = T.outer;
     I.relres = T.relres;
     int s = T.status;
-    if (T.mode != M_DONE) s = ctl_words[0] ? ctl_words[0] : (ctl_words[2] ? MVGD_ECANCELLED : MVGD_ENOCONV);
+    if (T.mode != M_DONE && s == MVGD_OK) s = MVGD_ENOCONV;
     I.status = s;
     I.reserved = 0;
     out[q] = I;
 }
 
-__global__ void k_gather_rows(const double* __restrict__ src, const int32_t* __restrict__ order, int64_t n, int Q,
-                              double* __restrict__ dst) {
+__global__ void k_scatter_solution(const Prob* P, double* __restrict__ dst) {
+    const int64_t n = P->n;
+    const int Q = P->Q;
+    const int32_t* order = P->order;
+    const double* src = P->u;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * Q; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / Q, q = e % Q;
-        dst[e] = src[(int64_t)order[r] * Q + q];
+        const int64_t r = e / Q, q = e % Q;
+        const int64_t to = order ? (int64_t)order[r] : r;
+        dst[to * Q + q] = src[e];
     }
 }
 
-__global__ void k_scatter_rows(const double* __restrict__ src, const int32_t* __restrict__ order, int64_t n, int Q,
-                               double* __restrict__ dst) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * Q; e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r = e / Q, q = e % Q;
-        dst[(int64_t)order[r] * Q + q] = src[e];
-    }
-}
-
-struct SolveLayout {
-    Prob* prob;
-    int* chunk_prob;
-    RhsState* st;
-    double* part;
-    unsigned* arrive;
-    unsigned* bar;
-    int* ctl_words;
-    mvgd_solve_info* info;
-    double* fs;
-    double* us;
-    double* r64;
-    void* vec[9];  // x r rh p0 p1 v0 v1 s t
-    size_t bytes;
+constexpr int kTableMax = 256;
+struct TableArgs {
+    const Prob* prob[kTableMax];
+    int nchunk[kTableMax];
+    int count;
+    int first_chunk;
 };
 
-SolveLayout solve_layout(void* ws, int64_t n, int Q, int prec) {
-    SolveLayout L;
-    Carver cv(ws);
-    const int64_t nchunk = (n + kCh - 1) / kCh;
-    const size_t vt = prec == MVGD_FP64 ? sizeof(double) : sizeof(float);
-    L.prob = cv.take<Prob>(1);
-    L.chunk_prob = cv.take<int>(nchunk);
-    L.st = cv.take<RhsState>(Q);
-    L.part = cv.take<double>(3 * kChan * nchunk * Q);
-    L.arrive = cv.take<unsigned>(3);
-    L.bar = cv.take<unsigned>(2);
-    L.ctl_words = cv.take<int>(4);
-    L.info = cv.take<mvgd_solve_info>(Q);
-    L.fs = cv.take<double>(n * Q);
-    L.us = cv.take<double>(n * Q);
-    L.r64 = cv.take<double>(n * Q);
-    for (int v = 0; v < 9; v++) L.vec[v] = cv.take<char>(vt * n * Q);
-    L.bytes = cv.used;
-    return L;
+// Request and chunk tables from by-value parameters (capturable in a graph);
+// the first group also resets the barrier and the control words.
+__global__ void k_build_table(TableArgs A, int base, const Prob** prob, int* chunk_req, int* chunk_base,
+                              unsigned* bar, int* words, int first_group) {
+    __shared__ int start[kTableMax + 1];
+    if (threadIdx.x == 0) {
+        start[0] = A.first_chunk;
+        for (int i = 0; i < A.count; i++) start[i + 1] = start[i] + A.nchunk[i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < A.count; i += blockDim.x) {
+        prob[base + i] = A.prob[i];
+        chunk_base[base + i] = start[i];
+    }
+    for (int i = 0; i < A.count; i++)
+        for (int c = start[i] + threadIdx.x; c < start[i + 1]; c += blockDim.x) chunk_req[c] = base + i;
+    if (first_group && threadIdx.x == 0) {
+        bar[0] = 0;
+        bar[1] = 0;
+        words[0] = 0;  // err
+        words[3] = 0;  // stop
+    }
+}
+
+// Counts running and restarting right-hand sides of the listed requests.
+__global__ void k_count_active(const Prob** prob, int count, int* words) {
+    __shared__ int act, rst;
+    if (threadIdx.x == 0) { act = 0; rst = 0; }
+    __syncthreads();
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const Prob* P = prob[i];
+        for (int q = 0; q < P->Q; q++) {
+            const int md = __ldcg(&P->st[q].mode);
+            if (md != M_DONE) atomicAdd(&act, 1);
+            if (md == M_RESTART) atomicAdd(&rst, 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        words[1] = act;
+        words[2] = rst;
+    }
+}
+
+// After a launch that a cancel word or a barrier time-out ended, mark the
+// right-hand sides that did not finish.
+__global__ void k_mark_exit(const Prob** prob, int count, const int* words) {
+    const int err = words[0], stop = words[3];
+    if (!err && !stop) return;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const Prob* P = prob[i];
+        for (int q = 0; q < P->Q; q++)
+            if (P->st[q].mode != M_DONE) P->st[q].status = err ? err : MVGD_ECANCELLED;
+    }
+}
+
+// done[i] = 1 when every right-hand side of request i has finished.
+__global__ void k_poll(TableArgs A, int32_t* done) {
+    for (int i = threadIdx.x; i < A.count; i += blockDim.x) {
+        const Prob* P = A.prob[i];
+        int all = 1;
+        for (int q = 0; q < P->Q; q++) all &= (__ldcg(&P->st[q].mode) == M_DONE);
+        done[i] = all;
+    }
 }
 
 template <bool MIXED, int QT>
-mvgd_status launch_solve(const Prob* dprob, const int* chunk_prob, int nchunks, Ctl ctl, int budget,
-                         cudaStream_t s) {
+mvgd_status launch_solve(ReqTable tab, int nchunks, Ctl ctl, int budget, cudaStream_t s) {
     auto fn = k_solve<MIXED, QT>;
     int dev = 0, sms = 0, per_sm = 0;
     MVGD_CUDA_TRY(cudaGetDevice(&dev));
@@ -548,80 +806,75 @@ mvgd_status launch_solve(const Prob* dprob, const int* chunk_prob, int nchunks, 
     if (per_sm < 1) return MVGD_ECUDA;
     int grid = sms * per_sm;
     if (grid > nchunks) grid = nchunks;
-    void* args[] = {(void*)&dprob, (void*)&chunk_prob, (void*)&nchunks, (void*)&ctl, (void*)&budget};
+    void* args[] = {(void*)&tab, (void*)&nchunks, (void*)&ctl, (void*)&budget};
     MVGD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, 0, s));
     return MVGD_OK;
 }
 
 template <bool MIXED>
-mvgd_status dispatch_q(int Q, const Prob* dprob, const int* chunk_prob, int nchunks, Ctl ctl, int budget,
-                       cudaStream_t s) {
-    if (Q <= 1) return launch_solve<MIXED, 1>(dprob, chunk_prob, nchunks, ctl, budget, s);
-    if (Q <= 2) return launch_solve<MIXED, 2>(dprob, chunk_prob, nchunks, ctl, budget, s);
-    if (Q <= 4) return launch_solve<MIXED, 4>(dprob, chunk_prob, nchunks, ctl, budget, s);
-    return launch_solve<MIXED, 8>(dprob, chunk_prob, nchunks, ctl, budget, s);
+mvgd_status dispatch_q(int Q, ReqTable tab, int nchunks, Ctl ctl, int budget, cudaStream_t s) {
+    if (Q <= 1) return launch_solve<MIXED, 1>(tab, nchunks, ctl, budget, s);
+    if (Q <= 2) return launch_solve<MIXED, 2>(tab, nchunks, ctl, budget, s);
+    if (Q <= 4) return launch_solve<MIXED, 4>(tab, nchunks, ctl, budget, s);
+    return launch_solve<MIXED, 8>(tab, nchunks, ctl, budget, s);
 }
 
-__global__ void k_fill_chunks(int* chunk_prob, int nchunk, int value) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunk; c += gridDim.x * blockDim.x) chunk_prob[c] = value;
+int gather_blocks(int64_t elems) {
+    int64_t gb = (elems + 255) / 256;
+    return (int)(gb > 8192 ? 8192 : (gb < 1 ? 1 : gb));
 }
+
+int64_t max_chunks_for(int count, int64_t total_rows) { return total_rows / kCh + count + 1; }
 
 }  // namespace
 }  // namespace mvgd
 
 using namespace mvgd;
 
-MVGD_API size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec) {
+// ---------------------------------------------------------------------------------
+// Requests
+// ---------------------------------------------------------------------------------
+MVGD_API size_t mvgd_request_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec) {
     (void)k;
     if (n <= 0 || nrhs < 1 || nrhs > 8) return 0;
-    return solve_layout(nullptr, n, nrhs, prec).bytes;
+    return req_layout(nullptr, n, nrhs, prec).bytes;
 }
 
-MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, const double* f, double* u,
-                                const mvgd_solve_opts* opts, mvgd_solve_info* info, const int32_t* cancel,
-                                void* ws, size_t ws_bytes, mvgd_stream_t stream) {
-    if (!L || !f || !u || !opts || !info || !ws || nrhs < 1 || nrhs > 8) return MVGD_EINVAL;
+MVGD_API mvgd_status mvgd_request_init(void* req_ws, size_t req_bytes, const mvgd_ell* L, int32_t nrhs, double sigma,
+                                       const double* f, const double* u0, const mvgd_solve_opts* opts,
+                                       mvgd_stream_t stream) {
+    if (!req_ws || !L || !f || !opts || nrhs < 1 || nrhs > 8) return MVGD_EINVAL;
     if (L->n < 2 || L->n >= (1ll << 31) || L->k < kMinK || L->k > kMaxK || !L->col || !L->val) return MVGD_EINVAL;
     if (L->prec != MVGD_FP64 && L->prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
     if (L->prec == MVGD_FP32_REFINE && !L->val_lo) return MVGD_EINVAL;
-    if (!aligned(f) || !aligned(u) || !aligned(ws) || !aligned(L->col) || !aligned(L->val) || !aligned(L->val_lo) ||
-        !aligned(L->order))
+    if (!aligned(f) || !aligned(u0) || !aligned(req_ws) || !aligned(L->col) || !aligned(L->val) ||
+        !aligned(L->val_lo) || !aligned(L->order))
         return MVGD_EINVAL;
     if (!(opts->rtol > 0) || opts->maxit < 1 || !(sigma == sigma)) return MVGD_EINVAL;
     const bool mixed = L->prec == MVGD_FP32_REFINE;
     if (mixed && (opts->inner_maxit < 1 || !(opts->inner_rtol > 0) || opts->max_outer < 1)) return MVGD_EINVAL;
     const int64_t n = L->n;
-    const int Q = nrhs;
-    SolveLayout W = solve_layout(ws, n, Q, L->prec);
-    if (ws_bytes < W.bytes) return MVGD_EWORKSPACE;
+    ReqLayout W = req_layout(req_ws, n, nrhs, L->prec);
+    if (req_bytes < W.bytes) return MVGD_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-
-    cudaPointerAttributes pa;
-    MVGD_CUDA_TRY(cudaPointerGetAttributes(&pa, info));
-    const bool host_info = pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged;
-
-    const double* fs = f;
-    double* us = u;
-    if (L->order) {
-        int gb = (int)((n * Q + 255) / 256);
-        if (gb > 8192) gb = 8192;
-        k_gather_rows<<<gb, 256, 0, s>>>(f, L->order, n, Q, W.fs);
-        k_gather_rows<<<gb, 256, 0, s>>>(u, L->order, n, Q, W.us);
-        fs = W.fs;
-        us = W.us;
-    }
-    const int nchunk = (int)((n + kCh - 1) / kCh);
+    const int gb = gather_blocks(n * nrhs);
+    k_gather_rows<<<gb, 256, 0, s>>>(f, L->order, n, nrhs, W.fs, 0);
+    k_gather_rows<<<gb, 256, 0, s>>>(u0, L->order, n, nrhs, W.us, u0 == nullptr);
     Prob P;
     P.n = n;
     P.k = L->k;
-    P.Q = Q;
+    P.Q = nrhs;
+    P.prec = L->prec;
+    P.precond = opts->precond == 1 ? 1 : 0;
     P.sigma = sigma;
     P.col = L->col;
     P.val = L->val;
     P.val_lo = L->val_lo;
-    P.f = fs;
-    P.u = us;
-    P.x = mixed ? W.vec[0] : (void*)us;
+    P.order = L->order;
+    P.f = W.fs;
+    P.u = W.us;
+    P.x = mixed ? W.vec[0] : (void*)W.us;
+    P.xb = W.vec[9];
     P.r = W.vec[1];
     P.rh = W.vec[2];
     P.p[0] = W.vec[3];
@@ -631,47 +884,159 @@ MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, c
     P.s = W.vec[7];
     P.t = W.vec[8];
     P.r64 = W.r64;
+    P.invd = W.invd;
     P.st = W.st;
     P.part = W.part;
     P.arrive = W.arrive;
-    P.chunk0 = 0;
-    P.nchunk = nchunk;
+    P.nchunk = (int)((n + kCh - 1) / kCh);
+    P.pad = 0;
     P.rtol = opts->rtol;
     P.inner_rtol = mixed ? opts->inner_rtol : 0.0;
     P.maxit = opts->maxit;
     P.inner_maxit = mixed ? opts->inner_maxit : opts->maxit;
     P.max_outer = mixed ? opts->max_outer : 1000;
-    P.precond = opts->precond == 1 ? 1 : 0;
-    MVGD_CUDA_TRY(cudaMemcpyAsync(W.prob, &P, sizeof(Prob), cudaMemcpyHostToDevice, s));
-    k_fill_chunks<<<(nchunk + 255) / 256, 256, 0, s>>>(W.chunk_prob, nchunk, 0);
-    k_init_states<<<1, 32, 0, s>>>(W.st, Q, W.arrive, W.bar, W.ctl_words, Q);
+    P.pad2 = 0;
+    k_request_init<<<1, 32, 0, s>>>(P, W.prob, n);
+    if (P.precond) k_prep_scaling<<<gather_blocks(n), 256, 0, s>>>(P);
+    return launch_status();
+}
 
+MVGD_API size_t mvgd_iterate_workspace_bytes(int32_t max_requests, int64_t max_total_rows) {
+    if (max_requests < 1 || max_total_rows < 1) return 0;
+    return ctl_layout(nullptr, max_requests, max_chunks_for(max_requests, max_total_rows)).bytes;
+}
+
+MVGD_API mvgd_status mvgd_iterate(void* const* reqs, const int64_t* req_rows, const int32_t* req_nrhs, int32_t count,
+                                  int32_t prec, int32_t max_iterations, const int32_t* cancel, void* ctl_ws,
+                                  size_t ctl_bytes, mvgd_stream_t stream) {
+    if (!reqs || !req_rows || !req_nrhs || count < 1 || count > kMaxReq || max_iterations < 0 || !ctl_ws)
+        return MVGD_EINVAL;
+    if (prec != MVGD_FP64 && prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    int64_t total_rows = 0;
+    int maxQ = 1;
+    for (int i = 0; i < count; i++) {
+        if (!reqs[i] || !aligned(reqs[i]) || req_rows[i] < 1 || req_rows[i] >= (1ll << 31) || req_nrhs[i] < 1 ||
+            req_nrhs[i] > 8)
+            return MVGD_EINVAL;
+        total_rows += req_rows[i];
+        if (req_nrhs[i] > maxQ) maxQ = req_nrhs[i];
+    }
+    if (!aligned(ctl_ws) || !aligned(cancel)) return MVGD_EINVAL;
+    if (ctl_bytes < mvgd_iterate_workspace_bytes(count, total_rows)) return MVGD_EWORKSPACE;
+    if (max_iterations == 0) return MVGD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    CtlLayout C = ctl_layout(ctl_ws, count, max_chunks_for(count, total_rows));
+    int nchunks = 0;
+    for (int g = 0; g < count; g += kTableMax) {
+        TableArgs A;
+        A.count = count - g < kTableMax ? count - g : kTableMax;
+        A.first_chunk = nchunks;
+        for (int i = 0; i < A.count; i++) {
+            A.prob[i] = reinterpret_cast<const Prob*>(reqs[g + i]);  // the Prob record opens every request workspace
+            A.nchunk[i] = (int)((req_rows[g + i] + kCh - 1) / kCh);
+            nchunks += A.nchunk[i];
+        }
+        k_build_table<<<1, 256, 0, s>>>(A, g, C.prob, C.chunk_req, C.chunk_base, C.bar, C.words, g == 0);
+    }
+    k_count_active<<<1, 256, 0, s>>>(C.prob, count, C.words);
     Ctl ctl;
-    ctl.bar.count = W.bar;
-    ctl.bar.gen = W.bar + 1;
-    ctl.err = W.ctl_words;
-    ctl.active = W.ctl_words + 1;
-    ctl.stop = W.ctl_words + 2;
+    ctl.bar.count = C.bar;
+    ctl.bar.gen = C.bar + 1;
+    ctl.err = C.words;
+    ctl.active = C.words + 1;
+    ctl.nrestart = C.words + 2;
+    ctl.stop = C.words + 3;
     ctl.cancel = cancel;
     ctl.limit = 20000000ll;  // polls of >= 32 ns each: seconds, never reached by co-resident blocks
-    // every inner iteration and every restart is one pass of the three phases
-    long long budget = (long long)opts->maxit + 2ll * (P.max_outer + 2) + 4;
-    if (budget > (1ll << 30)) budget = 1ll << 30;
-    mvgd_status st = mixed ? dispatch_q<true>(Q, W.prob, W.chunk_prob, nchunk, ctl, (int)budget, s)
-                           : dispatch_q<false>(Q, W.prob, W.chunk_prob, nchunk, ctl, (int)budget, s);
+    ReqTable tab;
+    tab.prob = C.prob;
+    tab.chunk_req = C.chunk_req;
+    tab.chunk_base = C.chunk_base;
+    mvgd_status st = prec == MVGD_FP32_REFINE ? dispatch_q<true>(maxQ, tab, nchunks, ctl, max_iterations, s)
+                                              : dispatch_q<false>(maxQ, tab, nchunks, ctl, max_iterations, s);
     if (st != MVGD_OK) return st;
-    if (L->order) {
-        int gb = (int)((n * Q + 255) / 256);
-        if (gb > 8192) gb = 8192;
-        k_scatter_rows<<<gb, 256, 0, s>>>(W.us, L->order, n, Q, u);
+    k_mark_exit<<<1, 256, 0, s>>>(C.prob, count, C.words);
+    return launch_status();
+}
+
+MVGD_API mvgd_status mvgd_request_poll(void* const* reqs, int32_t count, int32_t* done, mvgd_stream_t stream) {
+    if (!reqs || count < 1 || !done || !aligned(done)) return MVGD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int g = 0; g < count; g += kTableMax) {
+        TableArgs A;
+        A.count = count - g < kTableMax ? count - g : kTableMax;
+        A.first_chunk = 0;
+        for (int i = 0; i < A.count; i++) {
+            if (!reqs[g + i] || !aligned(reqs[g + i])) return MVGD_EINVAL;
+            A.prob[i] = reinterpret_cast<const Prob*>(reqs[g + i]);
+            A.nchunk[i] = 0;
+        }
+        k_poll<<<1, 256, 0, s>>>(A, done + g);
     }
-    k_finish<<<1, 32, 0, s>>>(W.st, Q, W.ctl_words, host_info ? W.info : info);
-    MVGD_CUDA_TRY(cudaGetLastError());
+    return launch_status();
+}
+
+MVGD_API mvgd_status mvgd_request_finish(void* req_ws, int64_t n, int32_t nrhs, double* u, mvgd_solve_info* info,
+                                         mvgd_stream_t stream) {
+    if (!req_ws || !u || !info || n < 1 || nrhs < 1 || nrhs > 8) return MVGD_EINVAL;
+    if (!aligned(req_ws) || !aligned(u)) return MVGD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Prob* P = reinterpret_cast<const Prob*>(req_ws);
+    k_scatter_solution<<<gather_blocks(n * nrhs), 256, 0, s>>>(P, u);
+    k_finish<<<1, 32, 0, s>>>(P, info);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------------
+// One system: init + iterate to the end + finish
+// ---------------------------------------------------------------------------------
+MVGD_API size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec) {
+    if (n <= 0 || nrhs < 1 || nrhs > 8) return 0;
+    return mvgd_request_workspace_bytes(n, k, nrhs, prec) + mvgd_iterate_workspace_bytes(1, n) +
+           align_up(sizeof(mvgd_solve_info) * 8);
+}
+
+MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, const double* f, double* u,
+                                const mvgd_solve_opts* opts, mvgd_solve_info* info, const int32_t* cancel,
+                                void* ws, size_t ws_bytes, mvgd_stream_t stream) {
+    if (!L || !f || !u || !opts || !info || !ws || nrhs < 1 || nrhs > 8) return MVGD_EINVAL;
+    if (L->n < 2 || L->n >= (1ll << 31) || L->k < kMinK || L->k > kMaxK || !L->col || !L->val) return MVGD_EINVAL;
+    if (L->prec != MVGD_FP64 && L->prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    if (!(opts->rtol > 0) || opts->maxit < 1 || !(sigma == sigma)) return MVGD_EINVAL;
+    if (L->prec == MVGD_FP32_REFINE &&
+        (!L->val_lo || opts->inner_maxit < 1 || !(opts->inner_rtol > 0) || opts->max_outer < 1))
+        return MVGD_EINVAL;
+    const size_t need = mvgd_solve_workspace_bytes(L->n, L->k, nrhs, L->prec);
+    if (!aligned(ws) || !aligned(u) || !aligned(f)) return MVGD_EINVAL;
+    if (ws_bytes < need) return MVGD_EWORKSPACE;
+    cudaPointerAttributes pa;
+    MVGD_CUDA_TRY(cudaPointerGetAttributes(&pa, info));
+    const bool host_info = pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged;
+    char* base = static_cast<char*>(ws);
+    const size_t req_bytes = mvgd_request_workspace_bytes(L->n, L->k, nrhs, L->prec);
+    const size_t ctl_bytes = mvgd_iterate_workspace_bytes(1, L->n);
+    void* req = base;
+    void* ctl = base + req_bytes;
+    mvgd_solve_info* staged = reinterpret_cast<mvgd_solve_info*>(base + req_bytes + ctl_bytes);
+    mvgd_status st = mvgd_request_init(req, req_bytes, L, nrhs, sigma, f, u, opts, stream);
+    if (st != MVGD_OK) return st;
+    // every inner iteration and every restart is one pass of the phases
+    const bool mixed = L->prec == MVGD_FP32_REFINE;
+    long long budget = (long long)opts->maxit + 2ll * ((mixed ? opts->max_outer : 1000) + 2) + 4;
+    if (budget > (1ll << 30)) budget = 1ll << 30;
+    int64_t rows = L->n;
+    int32_t q = nrhs;
+    void* reqs[1] = {req};
+    st = mvgd_iterate(reqs, &rows, &q, 1, L->prec, (int32_t)budget, cancel, ctl, ctl_bytes, stream);
+    if (st != MVGD_OK) return st;
+    st = mvgd_request_finish(req, L->n, nrhs, u, host_info ? staged : info, stream);
+    if (st != MVGD_OK) return st;
     if (!host_info) return MVGD_OK;
-    MVGD_CUDA_TRY(cudaMemcpyAsync(info, W.info, sizeof(mvgd_solve_info) * Q, cudaMemcpyDeviceToHost, s));
+    cudaStream_t s = (cudaStream_t)stream;
+    MVGD_CUDA_TRY(cudaMemcpyAsync(info, staged, sizeof(mvgd_solve_info) * nrhs, cudaMemcpyDeviceToHost, s));
     MVGD_CUDA_TRY(cudaStreamSynchronize(s));
     int worst = MVGD_OK;
-    for (int q = 0; q < Q; q++)
-        if (info[q].status != MVGD_OK && worst == MVGD_OK) worst = info[q].status;
+    for (int i = 0; i < nrhs; i++)
+        if (info[i].status != MVGD_OK && worst == MVGD_OK) worst = info[i].status;
     return (mvgd_status)worst;
 }
