@@ -72,6 +72,23 @@ mvgd_status mvgd_knn(const double *pts, int64_t n, int32_t k, int32_t *nbr, int3
                      double cell_size, void *workspace, size_t workspace_bytes,
                      mvgd_stream_t stream);
 
+/* The same kNN for callers that cannot allocate device memory -- code being
+ * recorded into a CUDA graph, where a cudaMalloc would break the capture;
+ * loops that must never wait on the allocator; host frameworks that own every
+ * device buffer and pass only inputs and outputs.  (The paper has no
+ * counterpart: this is an interface variant, not part of the method.)
+ * The call allocates nothing: its scratch is one static device array of the
+ * library, sized for MVGD_KNN_NOALLOC_MAX_POINTS points and held by every GPU
+ * that loads the library until the process exits.  n above that maximum
+ * returns MVGD_EINVAL before touching the device.  The first call on a device
+ * looks up the array's device address (set-up, once per device), so make it
+ * before any stream capture.  All calls on a device share the array: calls
+ * whose work may overlap on the GPU (unordered streams) race on it and must be
+ * serialised by the caller.  Results are identical to mvgd_knn. */
+#define MVGD_KNN_NOALLOC_MAX_POINTS 65536
+mvgd_status mvgd_knn_noalloc(const double *pts, int64_t n, int32_t k, int32_t *nbr, int32_t *order,
+                             double cell_size, mvgd_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Assembly -- Sec. 2 and Sec. 3.1.  Row i of L approximates the LB operator at
  * p_i as a combination of U_i and the values at its k neighbours:

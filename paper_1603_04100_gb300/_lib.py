@@ -102,6 +102,8 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_assemble_batch.restype = C.c_int
     L.mvgd_request_poll.argtypes = [C.POINTER(C.c_void_p), C.c_int32, _P, _P]
     L.mvgd_request_poll.restype = C.c_int
+    L.mvgd_knn_noalloc.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, C.c_double, _P]
+    L.mvgd_knn_noalloc.restype = C.c_int
     _lib = L
     return L
 

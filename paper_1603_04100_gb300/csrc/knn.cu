@@ -21,6 +21,7 @@
 //      candidate can have given the FP32 error bound (else the scan is redone
 //      with exact keys).  Both bounds are evaluated with directed rounding.
 #include <cfloat>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -589,4 +590,63 @@ MVGD_API mvgd_status mvgd_knn(const double* pts, int64_t n, int32_t k, int32_t* 
                                                  L.pcell, nbr);
     if (order) MVGD_CUDA_TRY(cudaMemcpyAsync(order, L.order, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
     return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// kNN for callers that cannot allocate device memory.
+//
+// Some callers of this library may not call cudaMalloc at all: code that is
+// being recorded into a CUDA graph (an allocation would break the capture),
+// latency-bound loops that must never wait on the allocator, and host
+// applications or plug-in frameworks that own every device buffer and hand
+// the library only its inputs and outputs.  For them the scratch that
+// mvgd_knn takes from a caller workspace lives instead in one file-scope
+// device array, reserved when the library's code is loaded on a GPU and held
+// by every GPU that loads it until the process exits.  The array is sized for
+// MVGD_KNN_NOALLOC_MAX_POINTS points; larger clouds are refused.
+//
+// In host code the array's name is only a host-side stand-in, never a device
+// address, so its address is fetched with cudaGetSymbolAddress once per
+// device, with that device current, on the first call made on that device;
+// that first call should therefore come before any stream capture.  Every
+// call on a device shares the one array: calls whose work overlaps on the GPU
+// (different streams, no ordering between them) race on it and must be
+// serialised by the caller.  The array keeps the last call's contents; the
+// kNN zeroes what it needs zeroed (bucket counts, occupancy bits) itself.
+// ---------------------------------------------------------------------------
+namespace mvgd {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // >= knn workspace of 65,536 points
+static __device__ __align__(256) unsigned char g_knn_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+mvgd_status scratch_for_current_device(void** out) {
+    int dev = 0;
+    MVGD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return MVGD_ECUDA;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_knn_scratch) != cudaSuccess || p == nullptr) return MVGD_ECUDA;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return MVGD_OK;
+}
+
+}  // namespace
+}  // namespace mvgd
+
+MVGD_API mvgd_status mvgd_knn_noalloc(const double* pts, int64_t n, int32_t k, int32_t* nbr, int32_t* order,
+                                      double cell_size, mvgd_stream_t stream) {
+    if (n > MVGD_KNN_NOALLOC_MAX_POINTS || knn_layout(nullptr, n).bytes > kNoAllocScratchBytes) return MVGD_EINVAL;
+    if (!pts || !nbr || n < 2 || k < 1 || k > kMaxK || k >= n) return MVGD_EINVAL;
+    void* scratch = nullptr;
+    mvgd_status st = scratch_for_current_device(&scratch);
+    if (st != MVGD_OK) return st;
+    return mvgd_knn(pts, n, k, nbr, order, cell_size, scratch, kNoAllocScratchBytes, stream);
 }
