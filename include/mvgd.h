@@ -237,12 +237,14 @@ mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const doub
  * caller-owned workspace; the operator L it was initialised with must stay
  * alive until mvgd_request_finish.  Results of a request do not depend on
  * which other requests share a launch: every reduction runs per request in a
- * fixed order over fixed 512-row chunks.
+ * fixed order over fixed 256-row chunks.
  *
  * mvgd_request_init: gathers f (and u0, or zeros if u0 == NULL) into stored
  *   order and sets every right-hand side to its first restart.  Asynchronous.
  * mvgd_iterate: advances the listed requests (host array of request
- *   workspaces, with their row and RHS counts; all of one precision) by at
+ *   workspaces, with their row, RHS and neighbour counts K -- the K of the
+ *   operator each was initialised with, 5..31, which sizes the launch's
+ *   shared-memory staging; all of one precision) by at
  *   most max_iterations Krylov iterations in one cooperative launch; requests
  *   whose right-hand sides are all done cost nothing.  ctl_ws (size from
  *   mvgd_iterate_workspace_bytes for at least this many requests and rows)
@@ -257,9 +259,9 @@ mvgd_status mvgd_request_init(void *req_workspace, size_t req_bytes, const mvgd_
                               double sigma, const double *f, const double *u0, const mvgd_solve_opts *opts,
                               mvgd_stream_t stream);
 size_t mvgd_iterate_workspace_bytes(int32_t max_requests, int64_t max_total_rows);
-mvgd_status mvgd_iterate(void *const *reqs, const int64_t *req_rows, const int32_t *req_nrhs, int32_t count,
-                         int32_t prec, int32_t max_iterations, const int32_t *cancel, void *ctl_workspace,
-                         size_t ctl_bytes, mvgd_stream_t stream);
+mvgd_status mvgd_iterate(void *const *reqs, const int64_t *req_rows, const int32_t *req_nrhs,
+                         const int32_t *req_k, int32_t count, int32_t prec, int32_t max_iterations,
+                         const int32_t *cancel, void *ctl_workspace, size_t ctl_bytes, mvgd_stream_t stream);
 mvgd_status mvgd_request_finish(void *req_workspace, int64_t n, int32_t nrhs, double *u,
                                 mvgd_solve_info *info, mvgd_stream_t stream);
 /* done (out, DEVICE int32 [count]): 1 where every right-hand side of the

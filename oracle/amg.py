@@ -1,0 +1,139 @@
+"""Aggregation multigrid for (sigma I - L) -- TEST INFRASTRUCTURE ONLY (FP64).
+
+The paper solves its MVGD systems with algebraic multigrid (Sec. 4.2 and the
+timing discussion of Sec. 5) but does not say which variant.  The CUDA path
+uses plain (unsmoothed) aggregation multigrid as a right preconditioner of
+BiCGSTAB; this module restates that preconditioner step by step from its
+definition, in FP64, so that the GPU hierarchy and V-cycle can be compared
+against it.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU leg may import it; it shares no code with the CUDA path.
+
+Definitions (Braess 1995 for plain aggregation; Baker, Falgout, Kolev and Yang
+2011 for the l1-Jacobi smoother):
+
+* level 0 is A = sigma I - L in the operator's stored row order;
+* an aggregate is `agg` consecutive rows of a level; the prolongation P is
+  piecewise constant (P[i, i // agg] = 1) and the next level is the Galerkin
+  product P^T A P, i.e. entry (I, J) is the sum of a_ij over rows i of
+  aggregate I and columns j of aggregate J;
+* coarsening stops at the first level with at most `coarsest` rows, which is
+  solved exactly (its dense inverse);
+* the smoother is one l1-Jacobi step x += D^-1 (b - A x), D_ii = sum_j |a_ij|;
+* one V-cycle on b: y = D^-1 b (pre-smoothing from zero), r = b - A y,
+  x_c = V-cycle of the next level on P^T r, x = y + P x_c, then one
+  post-smoothing step x += D^-1 (b - A x).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+AGG = 8
+COARSEST = 512
+
+
+class Level:
+    """One level: a sparse matrix as (rows, cols, vals) sorted by (row, col),
+    without duplicate entries, plus its l1 diagonal."""
+
+    def __init__(self, n: int, rows, cols, vals):
+        self.n = int(n)
+        key = np.asarray(rows, dtype=np.int64) * self.n + np.asarray(cols, dtype=np.int64)
+        uniq, inv = np.unique(key, return_inverse=True)
+        summed = np.zeros(uniq.shape[0])
+        np.add.at(summed, inv, np.asarray(vals, dtype=np.float64))
+        self.rows = uniq // self.n
+        self.cols = uniq % self.n
+        self.vals = summed
+        self.l1 = np.zeros(self.n)
+        np.add.at(self.l1, self.rows, np.abs(self.vals))
+
+    def matvec(self, x: np.ndarray) -> np.ndarray:
+        y = np.zeros(self.n)
+        np.add.at(y, self.rows, self.vals * x[self.cols])
+        return y
+
+    def dense(self) -> np.ndarray:
+        A = np.zeros((self.n, self.n))
+        A[self.rows, self.cols] = self.vals
+        return A
+
+    def width(self) -> int:
+        return int(np.bincount(self.rows, minlength=self.n).max()) if self.n else 0
+
+
+def fine_level(val: np.ndarray, nbr: np.ndarray, sigma: float = 1.0) -> Level:
+    """A = sigma I - L from the MVGD rows (slot 0 = the point itself)."""
+    n, k = nbr.shape
+    rows = np.repeat(np.arange(n), k + 1)
+    cols = np.concatenate([np.arange(n)[:, None], nbr.astype(np.int64)], axis=1).ravel()
+    vals = -np.asarray(val, dtype=np.float64).ravel()
+    rows = np.concatenate([rows, np.arange(n)])
+    cols = np.concatenate([cols, np.arange(n)])
+    vals = np.concatenate([vals, np.full(n, float(sigma))])
+    return Level(n, rows, cols, vals)
+
+
+def galerkin(A: Level, agg: int = AGG) -> Level:
+    """P^T A P for the piecewise-constant P over `agg` consecutive rows."""
+    nc = (A.n + agg - 1) // agg
+    return Level(nc, A.rows // agg, A.cols // agg, A.vals)
+
+
+def hierarchy(val, nbr, sigma: float = 1.0, agg: int = AGG, coarsest: int = COARSEST) -> list:
+    """Levels 0..m; the last one has at most `coarsest` rows."""
+    levels = [fine_level(val, nbr, sigma)]
+    while levels[-1].n > coarsest:
+        levels.append(galerkin(levels[-1], agg))
+    return levels
+
+
+def coarsest_inverse(levels) -> np.ndarray:
+    return np.linalg.inv(levels[-1].dense())
+
+
+def vcycle(levels, b: np.ndarray, agg: int = AGG, inv: np.ndarray | None = None, lvl: int = 0) -> np.ndarray:
+    """One V(1,1)-cycle applied to b (a vector of level `lvl`)."""
+    A = levels[lvl]
+    if lvl == len(levels) - 1:
+        X = coarsest_inverse(levels) if inv is None else inv
+        return X @ b
+    d = 1.0 / A.l1
+    y = d * b
+    r = b - A.matvec(y)
+    bc = np.zeros(levels[lvl + 1].n)
+    np.add.at(bc, np.arange(A.n) // agg, r)
+    xc = vcycle(levels, bc, agg, inv, lvl + 1)
+    x = y + xc[np.arange(A.n) // agg]
+    return x + d * (b - A.matvec(x))
+
+
+def bicgstab_right(levels, f: np.ndarray, rtol: float = 1e-8, maxit: int = 5000, agg: int = AGG):
+    """Right-preconditioned BiCGSTAB on the level-0 matrix with one V-cycle per
+    preconditioner application; returns (x, iterations, relative residual)."""
+    A = levels[0]
+    inv = coarsest_inverse(levels)
+    M = lambda v: vcycle(levels, v, agg, inv)
+    x = np.zeros_like(f)
+    r = f.copy()
+    rh = r.copy()
+    fn = np.linalg.norm(f)
+    rho = alpha = omega = 1.0
+    p = np.zeros_like(f)
+    v = np.zeros_like(f)
+    for it in range(1, maxit + 1):
+        rho1 = rh @ r
+        beta = (rho1 / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = M(p)
+        v = A.matvec(ph)
+        alpha = rho1 / (rh @ v)
+        s = r - alpha * v
+        sh = M(s)
+        t = A.matvec(sh)
+        omega = (t @ s) / (t @ t)
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        rho = rho1
+        if np.linalg.norm(r) <= rtol * fn:
+            break
+    return x, it, np.linalg.norm(f - A.matvec(x)) / fn

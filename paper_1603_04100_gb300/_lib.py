@@ -91,8 +91,8 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_request_init.restype = C.c_int
     L.mvgd_iterate_workspace_bytes.argtypes = [C.c_int32, C.c_int64]
     L.mvgd_iterate_workspace_bytes.restype = C.c_size_t
-    L.mvgd_iterate.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int32,
-                               C.c_int32, C.c_int32, _P, _P, C.c_size_t, _P]
+    L.mvgd_iterate.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_size_t, _P]
     L.mvgd_iterate.restype = C.c_int
     L.mvgd_request_finish.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, _P]
     L.mvgd_request_finish.restype = C.c_int

@@ -78,6 +78,7 @@ class BatchPipeline:
         self._reqs = (C.c_void_p * cnt)(*[s.req_ws.data_ptr() for s in self.slots])
         self._rows = (C.c_int64 * cnt)(*[s.n for s in self.slots])
         self._nrhs = (C.c_int32 * cnt)(*[s.nrhs for s in self.slots])
+        self._k = (C.c_int32 * cnt)(*[s.k for s in self.slots])
         self.graph = None
 
     @property
@@ -112,8 +113,9 @@ class BatchPipeline:
             c = slot.op.cstruct()
             LB.check("mvgd_request_init", L.mvgd_request_init(vp(slot.req_ws), slot.req_ws.numel(), C.byref(c),
                                                                slot.nrhs, 1.0, vp(f), None, C.byref(self.opts), s))
-        LB.check("mvgd_iterate", L.mvgd_iterate(self._reqs, self._rows, self._nrhs, len(self.slots), self.prec,
-                                                 self.budget, vp(cancel), vp(self.ctl_ws), self.ctl_ws.numel(), s))
+        LB.check("mvgd_iterate", L.mvgd_iterate(self._reqs, self._rows, self._nrhs, self._k, len(self.slots),
+                                                 self.prec, self.budget, vp(cancel), vp(self.ctl_ws),
+                                                 self.ctl_ws.numel(), s))
         for slot in self.slots:
             LB.check("mvgd_request_finish", L.mvgd_request_finish(vp(slot.req_ws), slot.n, slot.nrhs, vp(slot.u),
                                                                    vp(slot.info), s))

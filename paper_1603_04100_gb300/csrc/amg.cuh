@@ -1,0 +1,59 @@
+// Aggregation multigrid hierarchy of sigma I - L: the layout shared by its
+// set-up (amg.cu) and the V-cycle phases of the persistent solver (solve.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace mvgd {
+
+constexpr int kAmgAgg = MVGD_AMG_AGG;            // rows per aggregate (consecutive in stored order)
+constexpr int kAmgCoarsest = MVGD_AMG_COARSEST;  // a level this small is solved exactly
+constexpr int kAmgStride = MVGD_AMG_MAX_WIDTH;   // slots per coarse row in the sliced layout
+constexpr int kAmgMaxLevels = 12;
+
+// One level.  Level 0 is the operator itself: its neighbour columns (the
+// operator's `col`, K slots) and an FP32 copy of its weights ([n_pad][K+1],
+// slot 0 = the point itself), so that A x = sigma x_i - (w_0 x_i + sum_s w_s x_j).
+// Levels >= 1 hold A explicitly: per row `cnt` entries (column, value) sorted
+// by column, padded to the slice's widest row with (own index, 0).
+struct AmgLevel {
+    int64_t n;
+    int32_t* col;    // level >= 1: [n_pad][kAmgStride] sliced
+    float* val;      // level 0: [n_pad][K+1]; level >= 1: [n_pad][kAmgStride]
+    double* val64;   // level >= 1: FP64 values (the Galerkin sums before rounding)
+    int32_t* cnt;    // level >= 1: [n] entries per row
+    int32_t* sw;     // level >= 1: [n_pad / 32] widest row of each slice
+    float* dinv;     // [n] 1 / sum_j |a_ij|  (l1-Jacobi)
+};
+
+struct AmgHeader {
+    int32_t nlev;       // levels, the coarsest included (>= 1)
+    int32_t k;          // K of the operator
+    int32_t status;     // MVGD_OK, or why set-up failed (device-written)
+    int32_t width_max;  // widest coarse row (device-written)
+    int64_t n;          // rows of level 0
+    double sigma;
+    const int32_t* col0;  // the operator's columns (level 0)
+    AmgLevel lv[kAmgMaxLevels];
+    float* dense;       // [nc][nc] the coarsest level as a dense matrix (FP32, set-up scratch)
+    float* cinv;        // [nc][nc] its inverse, row-major
+    int32_t* piv;       // [nc] set-up scratch
+    int64_t nc;         // rows of the coarsest level
+    size_t bytes;       // whole hierarchy
+};
+
+// Level sizes for a fine size n: n_0 = n, n_{l+1} = ceil(n_l / kAmgAgg) while
+// n_l > kAmgCoarsest.  Returns the level count (0 if it would exceed the maximum).
+__host__ __device__ inline int amg_levels(int64_t n, int64_t* sizes) {
+    int l = 0;
+    int64_t m = n;
+    while (true) {
+        if (l >= kAmgMaxLevels) return 0;
+        if (sizes) sizes[l] = m;
+        l++;
+        if (m <= kAmgCoarsest) return l;
+        m = (m + kAmgAgg - 1) / kAmgAgg;
+    }
+}
+
+}  // namespace mvgd

@@ -35,12 +35,12 @@
 namespace mvgd {
 namespace {
 
-constexpr int kCh = 512;
+constexpr int kCh = 256;   // rows per tile: one per thread, 8 slices of 32
 constexpr int kThreads = 256;
-constexpr int kRowsPerThread = kCh / kThreads;
 constexpr int kChan = 2;
 constexpr int kRedSlots = 3;
 constexpr int kMaxReq = 1024;
+constexpr long long kStageWaitLimit = 1ll << 24;  // polls of an mbarrier: far beyond any copy's landing time
 
 enum Phase : int { P_PRE_A = 0, P_A = 1, P_PRE_B = 2, P_B = 3, P_C = 4, P_COUNT = 5 };
 enum Mode : int { M_RESTART = 0, M_INNER = 1, M_SKIP = 2, M_DONE = 3 };
@@ -171,19 +171,40 @@ __device__ __forceinline__ void c_row_f64(const Prob& P, int64_t r, const RhsSta
     }
 }
 
-// A / B for INNER right-hand sides: one operator application each.
-template <bool MIXED, int QT>
-__device__ __forceinline__ void spmv_row(const Prob& P, int64_t r, int ph, const RhsState* S, const bool (&on)[QT],
-                                         const float (&c1)[QT], const float (&c2)[QT], F2 (&af)[kChan][QT],
-                                         double (&ad)[kChan][QT]) {
+// Starts the copy of one 32-row slice of the operator -- its k column slots
+// and k+1 weight slots, each 32 consecutive words in the sliced layout, so two
+// contiguous runs -- into the warp's shared-memory buffer: one bulk
+// asynchronous copy per run, issued by lane 0, completing on the warp's
+// mbarrier.  The evict-first hint keeps the small, reused Krylov vectors in L2
+// while the operator streams past.
+template <typename VT>
+__device__ __forceinline__ void stage_slice(const Prob& P, int64_t slice, int* colS, VT* valS, uint64_t* bar,
+                                            uint64_t pol) {
+    const int k = P.k, m = k + 1;
+    __syncwarp();  // every lane has consumed the previous slice (its values fed the row sums)
+    if (lane_id() == 0) {
+        const uint32_t cb = (uint32_t)(kSlice * k * sizeof(int)), vb = (uint32_t)(kSlice * m * sizeof(VT));
+        mbar_expect_tx(bar, cb + vb);
+        bulk_g2s(colS, P.col + slice * (int64_t)(kSlice * k), cb, bar, pol);
+        bulk_g2s(valS, static_cast<const VT*>(P.val) + slice * (int64_t)(kSlice * m), vb, bar, pol);
+    }
+}
+
+// A / B for INNER right-hand sides: one operator application each, reading
+// the row's columns and weights from the warp's staged slice.  Called by every
+// lane of a staged warp (`valid`: the lane's row exists); the row's own loads
+// are issued before `landed()` waits for the slice, so they overlap the copy.
+template <bool MIXED, int QT, typename Landed>
+__device__ __forceinline__ void spmv_row(const Prob& P, int64_t r, bool valid, int ph, const RhsState* S,
+                                         const bool (&on)[QT], const float (&c1)[QT], const float (&c2)[QT],
+                                         F2 (&af)[kChan][QT], double (&ad)[kChan][QT], const int* colS,
+                                         const typename std::conditional<MIXED, float, double>::type* valS,
+                                         Landed&& landed) {
     using VT = typename std::conditional<MIXED, float, double>::type;
-    const int Q = P.Q, k = P.k, m = k + 1;
-    const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
-    const int64_t cb = (r / kSlice) * (int64_t)(kSlice * k) + (r % kSlice);
-    const VT* __restrict__ val = static_cast<const VT*>(P.val);
+    const int Q = P.Q, k = P.k;
+    const int lane = (int)(r % kSlice);
     const VT sig = (VT)P.sigma;
-    const VT w0 = val[vb];
-    const VT invd = P.precond ? static_cast<const VT*>(P.invd)[r] : (VT)1;
+    const VT invd = (valid && P.precond) ? static_cast<const VT*>(P.invd)[r] : (VT)1;
     // vectors written by other blocks during this kernel: plain (coherent) loads
     const VT* R = static_cast<const VT*>(P.r);
     const VT* RH = static_cast<const VT*>(P.rh);
@@ -201,17 +222,20 @@ __device__ __forceinline__ void spmv_row(const Prob& P, int64_t r, int ph, const
         if (MIXED) {
             vold[q] = static_cast<const VT*>(P.v[S[q].pp]);
             src[q] = static_cast<const VT*>(P.p[S[q].pp]);
-            si[q] = (ph == P_A) ? R[e] + (VT)c1[q] * (src[q][e] - (VT)c2[q] * vold[q][e])
-                                : R[e] - (VT)c1[q] * vold[q][e];
+            if (valid)
+                si[q] = (ph == P_A) ? R[e] + (VT)c1[q] * (src[q][e] - (VT)c2[q] * vold[q][e])
+                                    : R[e] - (VT)c1[q] * vold[q][e];
         } else {
             src[q] = static_cast<const VT*>(ph == P_A ? P.p[0] : P.s);
-            si[q] = src[q][e];
+            if (valid) si[q] = src[q][e];
         }
     }
-#pragma unroll 4
+    if (!landed() || !valid) return;  // landed() is warp-collective: every lane calls it
+    const VT w0 = valS[lane];
+#pragma unroll 8
     for (int sl = 0; sl < k; sl++) {
-        const int64_t j = P.col[cb + (int64_t)sl * kSlice];
-        const VT w = val[vb + (int64_t)(sl + 1) * kSlice];
+        const int64_t j = colS[sl * kSlice + lane];
+        const VT w = valS[(sl + 1) * kSlice + lane];
 #pragma unroll
         for (int q = 0; q < QT; q++) {
             if (!on[q]) continue;
@@ -445,13 +469,83 @@ struct ReqTable {
     const int* chunk_base;    // [count] first chunk of each request
 };
 
+template <typename VT>
+__host__ __device__ constexpr size_t stage_bytes_per_warp(int kmax) {
+    return (size_t)kSlice * kmax * sizeof(int) + (size_t)kSlice * (kmax + 1) * sizeof(VT);
+}
+
+// This block has finished `cnt` tiles of request P in a reducing phase: publish
+// them (one fence and one atomic per block and request), and if they were the
+// request's last tiles, sum all its tile partials in tile order and advance the
+// per-RHS state.
 template <bool MIXED, int QT>
-__global__ void __launch_bounds__(kThreads) k_solve(ReqTable tab, int nchunks, Ctl ctl, int iter_budget) {
+__device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int slot, int cnt, const RhsState* S,
+                                                    double (&fin)[kThreads / 32][kChan * QT],
+                                                    double (&tot)[kChan * QT], int* last, const Ctl& ctl) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) *last = (atomicAdd(&P.arrive[slot], (unsigned)cnt) + (unsigned)cnt == (unsigned)P.nchunk);
+    __syncthreads();
+    if (*last) {
+        __threadfence();
+        double acc[kChan * QT];
+#pragma unroll
+        for (int e = 0; e < kChan * QT; e++) acc[e] = 0.0;
+        for (int l = tid; l < P.nchunk; l += kThreads)
+#pragma unroll
+            for (int e = 0; e < kChan * QT; e++) {
+                const int ch = e / QT, q = e % QT;
+                if (q < P.Q) acc[e] += __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q]);
+            }
+#pragma unroll
+        for (int e = 0; e < kChan * QT; e++) {
+            const double v = warp_sum(acc[e]);
+            if (lane == 0) fin[wid][e] = v;
+        }
+        __syncthreads();
+        if (tid < kChan * QT) {
+            double v = 0.0;
+            for (int w = 0; w < kThreads / 32; w++) v += fin[w][tid];
+            tot[tid] = v;
+        }
+        __syncthreads();
+        if (tid < P.Q) {
+            RhsState T = S[tid];
+            advance<MIXED>(P, ph, T, tot[0 * QT + tid], tot[1 * QT + tid], ctl);
+            P.st[tid] = T;
+        }
+        if (tid == 0) P.arrive[slot] = 0;
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <bool MIXED, int QT>
+__global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2) k_solve(ReqTable tab, int nchunks, Ctl ctl, int iter_budget, int kmax) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
+    extern __shared__ __align__(16) unsigned char stage_smem[];
     __shared__ RhsState S[QT];
-    __shared__ double red[kThreads / 32][kChan * QT];
+    __shared__ double red[2][kThreads / 32][kChan * QT];
+    __shared__ double fin[kThreads / 32][kChan * QT];
     __shared__ double tot[kChan * QT];
     __shared__ int last;
+    __shared__ __align__(8) uint64_t stage_bar[kThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // this warp's slice buffer: kmax column slots, then kmax + 1 weight slots
+    const size_t warp_bytes = stage_bytes_per_warp<VT>(kmax);
+    int* colS = reinterpret_cast<int*>(stage_smem + wid * warp_bytes);
+    VT* valS = reinterpret_cast<VT*>(stage_smem + wid * warp_bytes + (size_t)kSlice * kmax * sizeof(int));
+    uint64_t* bar = &stage_bar[wid];
+    uint64_t pol = 0;
+    if (lane == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        pol = l2_evict_first_policy();
+    }
+    __syncthreads();
+    uint32_t parity = 0;   // phase of the warp's mbarrier that the next copy completes
+    bool stage_ok = true;  // false once a copy failed to land in time: no more copies are issued
 
     for (int it = 0; it < iter_budget; ++it) {
         // read after the last barrier of the previous iteration: identical in every block
@@ -460,47 +554,72 @@ __global__ void __launch_bounds__(kThreads) k_solve(ReqTable tab, int nchunks, C
             if (ph == P_PRE_A && !pre_a) continue;
             if (ph == P_PRE_B && MIXED) continue;
             const bool reduce = ph == P_A || ph == P_B || ph == P_C;
-            for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-                const int ri = tab.chunk_req[c];
+            const int slot = red_slot(ph);
+            int cur = -1, tiles = 0, rb = 0;
+            bool inner[QT], restart[QT];
+            bool any_inner = false, any_restart = false, all_done = true;
+            float c1[QT], c2[QT];
+            for (int c = blockIdx.x;; c += gridDim.x) {
+                const int ri = c < nchunks ? tab.chunk_req[c] : -1;
+                if (ri != cur) {
+                    // leaving request `cur`: publish this block's tiles of it
+                    if (cur >= 0 && reduce && tiles > 0)
+                        arrive_and_finalize<MIXED, QT>(*tab.prob[cur], ph, slot, tiles, S, fin, tot, &last, ctl);
+                    if (ri < 0) break;
+                    cur = ri;
+                    tiles = 0;
+                    __syncthreads();
+                    const Prob& P = *tab.prob[ri];
+                    // a K above the one the staging buffers were sized for (a wrong
+                    // req_k) would overrun shared memory: do no work and end the launch
+                    const bool fits = P.k <= kmax;
+                    if (!fits && tid == 0) atomicCAS(ctl.err, 0, (int)MVGD_EINVAL);
+                    if (tid < QT) {
+                        if (tid < P.Q && fits) load_state(S[tid], P.st + tid);
+                        else S[tid].mode = M_DONE;
+                    }
+                    __syncthreads();
+                    any_inner = any_restart = false;
+                    all_done = true;
+#pragma unroll
+                    for (int q = 0; q < QT; q++) {
+                        const int md = S[q].mode;
+                        inner[q] = md == M_INNER;
+                        restart[q] = md == M_RESTART;
+                        any_inner |= inner[q];
+                        any_restart |= restart[q];
+                        all_done &= (md == M_DONE);
+                        c1[q] = (float)(ph == P_A ? S[q].beta : S[q].alpha);
+                        c2[q] = (float)S[q].omega;
+                    }
+                }
+                if (all_done) continue;  // the whole request is finished: no work, no arrival
                 const Prob& P = *tab.prob[ri];
                 const int lc = c - tab.chunk_base[ri];
-                if (tid < QT) {
-                    if (tid < P.Q) load_state(S[tid], P.st + tid);
-                    else S[tid].mode = M_DONE;
-                }
-                __syncthreads();
-                bool inner[QT], restart[QT];
-                bool any_inner = false, any_restart = false, all_done = true;
-                float c1[QT], c2[QT];
-#pragma unroll
-                for (int q = 0; q < QT; q++) {
-                    const int md = S[q].mode;
-                    inner[q] = md == M_INNER;
-                    restart[q] = md == M_RESTART;
-                    any_inner |= inner[q];
-                    any_restart |= restart[q];
-                    all_done &= (md == M_DONE);
-                    c1[q] = (float)(ph == P_A ? S[q].beta : S[q].alpha);
-                    c2[q] = (float)S[q].omega;
-                }
-                if (all_done) {  // the whole request is finished: no work, no arrival
-                    __syncthreads();
-                    continue;
-                }
+                const int64_t r = (int64_t)lc * kCh + tid;
+                const int64_t slice = (int64_t)lc * (kCh / kSlice) + wid;
                 F2 af[kChan][QT];
                 double ad[kChan][QT];
 #pragma unroll
                 for (int ch = 0; ch < kChan; ch++)
 #pragma unroll
                     for (int q = 0; q < QT; q++) { af[ch][q].hi = 0.0f; af[ch][q].lo = 0.0f; ad[ch][q] = 0.0; }
-                const int64_t row0 = (int64_t)lc * kCh;
-                for (int j = 0; j < kRowsPerThread; ++j) {
-                    const int64_t r = row0 + (int64_t)j * kThreads + tid;
-                    if (r >= P.n) break;
+                // warp-uniform: lane 0 stages the whole slice and every lane waits for it
+                const bool staged = (ph == P_A || ph == P_B) && any_inner && slice * kSlice < P.n && stage_ok;
+                if (staged) {
+                    stage_slice<VT>(P, slice, colS, valS, bar, pol);
+                    spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, c1, c2, af, ad, colS, valS, [&]() {
+                        const bool ok = mbar_wait(bar, parity, kStageWaitLimit);
+                        parity ^= 1u;
+                        stage_ok = __all_sync(0xffffffffu, ok);
+                        if (!stage_ok && lane == 0) atomicCAS(ctl.err, 0, (int)MVGD_ETIMEOUT);
+                        return stage_ok;
+                    });
+                }
+                if (r < P.n) {
                     // a restart computes its residual in A and resets the Krylov vectors in C,
                     // so that its first inner step starts at the next iteration's A
                     if (ph == P_A || ph == P_B) {
-                        if (any_inner) spmv_row<MIXED, QT>(P, r, ph, S, inner, c1, c2, af, ad);
                         if (any_restart && ph == P_A) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
                     } else if (ph == P_C) {
                         if (any_inner) {
@@ -512,73 +631,41 @@ __global__ void __launch_bounds__(kThreads) k_solve(ReqTable tab, int nchunks, C
                         elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
                     }
                 }
-                if (!reduce) {
-                    __syncthreads();
-                    continue;
-                }
-                // block reduction in a fixed order: FP32 partials within the warp in FP32
+                if (!reduce) continue;
+                // tile partials in a fixed order: FP32 partials within the warp in FP32,
+                // then the 8 warps in order; `red` alternates so one barrier per tile suffices
 #pragma unroll
                 for (int ch = 0; ch < kChan; ch++)
 #pragma unroll
                     for (int q = 0; q < QT; q++) {
                         double v = f2_to_double(warp_sum_f2(af[ch][q]));
                         if (any_restart || !MIXED) v += warp_sum(ad[ch][q]);
-                        if (lane == 0) red[wid][ch * QT + q] = v;
+                        if (lane == 0) red[rb][wid][ch * QT + q] = v;
                     }
                 __syncthreads();
-                const int slot = red_slot(ph);
                 if (tid < kChan * QT) {
                     double v = 0.0;
-                    for (int w = 0; w < kThreads / 32; w++) v += red[w][tid];
+                    for (int w = 0; w < kThreads / 32; w++) v += red[rb][w][tid];
                     const int ch = tid / QT, q = tid % QT;
                     if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + lc) * P.Q + q] = v;
                 }
-                __threadfence();
-                __syncthreads();
-                if (tid == 0) last = (atomicAdd(&P.arrive[slot], 1u) == (unsigned)(P.nchunk - 1));
-                __syncthreads();
-                if (last) {
-                    __threadfence();
-                    double acc[kChan * QT];
-#pragma unroll
-                    for (int e = 0; e < kChan * QT; e++) acc[e] = 0.0;
-                    for (int l = tid; l < P.nchunk; l += kThreads)
-#pragma unroll
-                        for (int e = 0; e < kChan * QT; e++) {
-                            const int ch = e / QT, q = e % QT;
-                            if (q < P.Q)
-                                acc[e] += __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q]);
-                        }
-#pragma unroll
-                    for (int e = 0; e < kChan * QT; e++) {
-                        double v = warp_sum(acc[e]);
-                        if (lane == 0) red[wid][e] = v;
-                    }
-                    __syncthreads();
-                    if (tid < kChan * QT) {
-                        double v = 0.0;
-                        for (int w = 0; w < kThreads / 32; w++) v += red[w][tid];
-                        tot[tid] = v;
-                    }
-                    __syncthreads();
-                    if (tid < P.Q) {
-                        RhsState T = S[tid];
-                        advance<MIXED>(P, ph, T, tot[0 * QT + tid], tot[1 * QT + tid], ctl);
-                        P.st[tid] = T;
-                    }
-                    if (tid == 0) P.arrive[slot] = 0;
-                    __threadfence();
-                }
-                __syncthreads();
+                rb ^= 1;
+                tiles++;
             }
             // the stop word is written only before the last barrier of an iteration and
             // read only after it, so every block takes the same exit decision
             if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
                 *ctl.stop = 1;
-            if (!grid_sync(ctl.bar, ctl.err, ctl.limit)) return;
+            if (!grid_sync(ctl.bar, ctl.err, ctl.limit)) {
+                it = iter_budget;  // error exit, after the drain below
+                break;
+            }
         }
-        if (*(volatile int*)ctl.active == 0 || *(volatile int*)ctl.stop != 0) break;
+        if (it < iter_budget && (*(volatile int*)ctl.active == 0 || *(volatile int*)ctl.stop != 0)) break;
     }
+    // a copy that missed its wait may still be landing: give it one more bounded
+    // wait before the block's shared memory is released
+    if (!stage_ok) mbar_wait(bar, parity ^ 1u, kStageWaitLimit);
 }
 
 // ------------------------------------------------------------------------------
@@ -797,26 +884,29 @@ __global__ void k_poll(TableArgs A, int32_t* done) {
 }
 
 template <bool MIXED, int QT>
-mvgd_status launch_solve(ReqTable tab, int nchunks, Ctl ctl, int budget, cudaStream_t s) {
+mvgd_status launch_solve(ReqTable tab, int nchunks, Ctl ctl, int budget, int kmax, cudaStream_t s) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
     auto fn = k_solve<MIXED, QT>;
+    const size_t smem = stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp);
     int dev = 0, sms = 0, per_sm = 0;
     MVGD_CUDA_TRY(cudaGetDevice(&dev));
     MVGD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MVGD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, 0));
+    MVGD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MVGD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
     if (per_sm < 1) return MVGD_ECUDA;
     int grid = sms * per_sm;
     if (grid > nchunks) grid = nchunks;
-    void* args[] = {(void*)&tab, (void*)&nchunks, (void*)&ctl, (void*)&budget};
-    MVGD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, 0, s));
+    void* args[] = {(void*)&tab, (void*)&nchunks, (void*)&ctl, (void*)&budget, (void*)&kmax};
+    MVGD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, smem, s));
     return MVGD_OK;
 }
 
 template <bool MIXED>
-mvgd_status dispatch_q(int Q, ReqTable tab, int nchunks, Ctl ctl, int budget, cudaStream_t s) {
-    if (Q <= 1) return launch_solve<MIXED, 1>(tab, nchunks, ctl, budget, s);
-    if (Q <= 2) return launch_solve<MIXED, 2>(tab, nchunks, ctl, budget, s);
-    if (Q <= 4) return launch_solve<MIXED, 4>(tab, nchunks, ctl, budget, s);
-    return launch_solve<MIXED, 8>(tab, nchunks, ctl, budget, s);
+mvgd_status dispatch_q(int Q, ReqTable tab, int nchunks, Ctl ctl, int budget, int kmax, cudaStream_t s) {
+    if (Q <= 1) return launch_solve<MIXED, 1>(tab, nchunks, ctl, budget, kmax, s);
+    if (Q <= 2) return launch_solve<MIXED, 2>(tab, nchunks, ctl, budget, kmax, s);
+    if (Q <= 4) return launch_solve<MIXED, 4>(tab, nchunks, ctl, budget, kmax, s);
+    return launch_solve<MIXED, 8>(tab, nchunks, ctl, budget, kmax, s);
 }
 
 int gather_blocks(int64_t elems) {
@@ -906,20 +996,21 @@ MVGD_API size_t mvgd_iterate_workspace_bytes(int32_t max_requests, int64_t max_t
     return ctl_layout(nullptr, max_requests, max_chunks_for(max_requests, max_total_rows)).bytes;
 }
 
-MVGD_API mvgd_status mvgd_iterate(void* const* reqs, const int64_t* req_rows, const int32_t* req_nrhs, int32_t count,
-                                  int32_t prec, int32_t max_iterations, const int32_t* cancel, void* ctl_ws,
-                                  size_t ctl_bytes, mvgd_stream_t stream) {
-    if (!reqs || !req_rows || !req_nrhs || count < 1 || count > kMaxReq || max_iterations < 0 || !ctl_ws)
+MVGD_API mvgd_status mvgd_iterate(void* const* reqs, const int64_t* req_rows, const int32_t* req_nrhs,
+                                  const int32_t* req_k, int32_t count, int32_t prec, int32_t max_iterations,
+                                  const int32_t* cancel, void* ctl_ws, size_t ctl_bytes, mvgd_stream_t stream) {
+    if (!reqs || !req_rows || !req_nrhs || !req_k || count < 1 || count > kMaxReq || max_iterations < 0 || !ctl_ws)
         return MVGD_EINVAL;
     if (prec != MVGD_FP64 && prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
     int64_t total_rows = 0;
-    int maxQ = 1;
+    int maxQ = 1, kmax = kMinK;
     for (int i = 0; i < count; i++) {
         if (!reqs[i] || !aligned(reqs[i]) || req_rows[i] < 1 || req_rows[i] >= (1ll << 31) || req_nrhs[i] < 1 ||
-            req_nrhs[i] > 8)
+            req_nrhs[i] > 8 || req_k[i] < kMinK || req_k[i] > kMaxK)
             return MVGD_EINVAL;
         total_rows += req_rows[i];
         if (req_nrhs[i] > maxQ) maxQ = req_nrhs[i];
+        if (req_k[i] > kmax) kmax = req_k[i];
     }
     if (!aligned(ctl_ws) || !aligned(cancel)) return MVGD_EINVAL;
     if (ctl_bytes < mvgd_iterate_workspace_bytes(count, total_rows)) return MVGD_EWORKSPACE;
@@ -952,8 +1043,8 @@ MVGD_API mvgd_status mvgd_iterate(void* const* reqs, const int64_t* req_rows, co
     tab.prob = C.prob;
     tab.chunk_req = C.chunk_req;
     tab.chunk_base = C.chunk_base;
-    mvgd_status st = prec == MVGD_FP32_REFINE ? dispatch_q<true>(maxQ, tab, nchunks, ctl, max_iterations, s)
-                                              : dispatch_q<false>(maxQ, tab, nchunks, ctl, max_iterations, s);
+    mvgd_status st = prec == MVGD_FP32_REFINE ? dispatch_q<true>(maxQ, tab, nchunks, ctl, max_iterations, kmax, s)
+                                              : dispatch_q<false>(maxQ, tab, nchunks, ctl, max_iterations, kmax, s);
     if (st != MVGD_OK) return st;
     k_mark_exit<<<1, 256, 0, s>>>(C.prob, count, C.words);
     return launch_status();
@@ -1027,7 +1118,7 @@ MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, c
     int64_t rows = L->n;
     int32_t q = nrhs;
     void* reqs[1] = {req};
-    st = mvgd_iterate(reqs, &rows, &q, 1, L->prec, (int32_t)budget, cancel, ctl, ctl_bytes, stream);
+    st = mvgd_iterate(reqs, &rows, &q, &L->k, 1, L->prec, (int32_t)budget, cancel, ctl, ctl_bytes, stream);
     if (st != MVGD_OK) return st;
     st = mvgd_request_finish(req, L->n, nrhs, u, host_info ? staged : info, stream);
     if (st != MVGD_OK) return st;

@@ -61,6 +61,20 @@ def random_sphere(n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(g / np.linalg.norm(g, axis=1, keepdims=True))
 
 
+def morton_sorted(pts: np.ndarray, bits: int = 10) -> np.ndarray:
+    """The same points reordered along a Z-order curve of their bounding cube
+    (`bits` per axis, stable in the original index): consecutive points are
+    then spatial neighbours, as in the stored order the kNN step produces."""
+    lo = pts.min(axis=0)
+    span = float((pts.max(axis=0) - lo).max()) or 1.0
+    q = np.minimum(((pts - lo) / span * (1 << bits)).astype(np.int64), (1 << bits) - 1)
+    code = np.zeros(pts.shape[0], dtype=np.int64)
+    for b in range(bits):
+        for d in range(3):
+            code |= ((q[:, d] >> b) & 1) << (3 * b + d)
+    return np.ascontiguousarray(pts[np.argsort(code, kind="stable")])
+
+
 def ellipsoid(n: int, seed: int, axes=(1.0, 0.7, 0.4)) -> np.ndarray:
     """Random sphere points scaled by the semi-axes (a, b, c)."""
     return np.ascontiguousarray(random_sphere(n, seed) * np.asarray(axes, dtype=np.float64))

@@ -22,9 +22,14 @@ def main(argv):
     for _ in range(2):
         nbr, order = api.knn(pts, 20, want_order=True)
         op = api.assemble(pts, nbr, prec=prec, order=order)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
         r = api.solve(op, f, rtol=1e-8, precond=1, maxit=iters)
+        t1.record()
     torch.cuda.synchronize()
-    print("ok", r.iters, r.outer)
+    ms = t0.elapsed_time(t1)
+    its = r.iters[0]
+    print("ok", r.iters, r.outer, "solve %.3f ms, %.1f us per iteration" % (ms, 1e3 * ms / max(1, its)))
 
 
 if __name__ == "__main__":

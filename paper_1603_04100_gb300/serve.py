@@ -149,8 +149,9 @@ class Server:
         reqs = (C.c_void_p * cnt)(*[x.ws.data_ptr() for x in active])
         rows = (C.c_int64 * cnt)(*[x.req.n for x in active])
         nrhs = (C.c_int32 * cnt)(*[x.req.nrhs for x in active])
+        ks = (C.c_int32 * cnt)(*[x.req.k for x in active])
         with torch.cuda.stream(self.stream):
-            LB.check("mvgd_iterate", L.mvgd_iterate(reqs, rows, nrhs, cnt, self.prec, self.epoch_iters, None,
+            LB.check("mvgd_iterate", L.mvgd_iterate(reqs, rows, nrhs, ks, cnt, self.prec, self.epoch_iters, None,
                                                      vp(self.ctl_ws), self.ctl_bytes, s))
             LB.check("mvgd_request_poll", L.mvgd_request_poll(reqs, cnt, vp(self.done_dev), s))
             self.done_host[:cnt].copy_(self.done_dev[:cnt], non_blocking=True)
