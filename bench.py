@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--paths", default="fp32_refine+amg,fp64+amg,fp32_refine,fp64",
+                    help="comma list of <precision>[+amg] paths to time (the fastest is the headline)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -115,10 +117,11 @@ class ClockSampler:
 # ------------------------------------------------------------------------------
 # algorithmic bytes of the persistent solver (per row)
 # ------------------------------------------------------------------------------
-def solver_bytes_per_row(k: int, mixed: bool, iters: int, restarts: int) -> float:
-    """Unique bytes one launch of the persistent solver must move per row.
+def solver_bytes_per_row(k: int, mixed: bool, iters: int, restarts: int, amg_coarse: float | None = None) -> float:
+    """Unique bytes one launch of the persistent solver must move per fine row.
 
-    Mixed, per inner iteration (FP32 vectors, FP32 hi weights, int32 columns):
+    Row-scaled flow, mixed, per inner iteration (FP32 vectors, FP32 hi weights,
+    int32 columns):
       A: col 4k + val 4k + self weight 4 + r,p,v,rh 16 + write p,v 8
       B: col 4k + val 4k + self weight 4 + r,v 8 + write s,t 8
       C: x,p,s,t,r,rh 24 + write x,r 8                      -> 16k + 80
@@ -126,10 +129,42 @@ def solver_bytes_per_row(k: int, mixed: bool, iters: int, restarts: int) -> floa
       fold u += scale x 20; residual col 4k + hi,lo 8(k+1) + u,f 16 + r64 8;
       restart r64 8 + self weight 4 + r,rh,p0,p1,v0,v1,x 28  -> 12k + 92
     Plain FP64, per iteration 24k + 160; per restart 12k + 96.
+
+    Multigrid flow (amg_coarse = bytes per fine row of one V-cycle's levels >= 1,
+    including the coarsest solve), per iteration with V-cycle level 0 on FP32
+    weights:
+      V-cycle level 0: down col 4k + val 4(k+1) + b,y 4+vt + write r + b,y of
+        level 1 (1/8 each) 5; up col 4k + val 4(k+1) + y,r,d 12 + write x vt
+        -> 16k + 29 + 2 vt (+ amg_coarse), twice per iteration
+      mixed (vt 4): PRE_A r,p,v,d 16 + p,y 8; A 8k+4 + ph,rh 8 + v 4;
+        PRE_B r,v,d 12 + s,y 8; B 8k+4 + sh,s 8 + t 4; C x,ph,sh,s,t,rh 24 + x,r 8;
+        two V-cycles 32k + 74                        -> 48k + 182 + 2 amg_coarse
+      FP64 (vt 8): PRE_A 40; A 12k+8 + 16 + 8; PRE_B 32; B 12k+8 + 16 + 8;
+        C 48 + 16; two V-cycles 32k + 90             -> 56k + 290 + 2 amg_coarse
     """
+    if amg_coarse is not None:
+        per = (48 * k + 182) if mixed else (56 * k + 290)
+        return iters * (per + 2 * amg_coarse) + restarts * ((12 * k + 92) if mixed else (12 * k + 96))
     if mixed:
         return iters * (16 * k + 80) + restarts * (12 * k + 92)
     return iters * (24 * k + 160) + restarts * (12 * k + 96)
+
+
+def amg_coarse_bytes(H, n: int) -> float:
+    """Bytes per fine row that one V-cycle moves on levels >= 1: per level, down
+    and up read each stored entry (int32 column + FP32 value) once, plus about
+    36 bytes of vectors per row; the coarsest solve reads its dense FP32 inverse."""
+    total = 0.0
+    for lv in range(1, H.levels):
+        cnt = H.level_rows(lv)[0] if lv < H.levels - 1 else None
+        info = H.info(lv)
+        if lv < H.levels - 1:
+            total += 16.0 * float(cnt.sum()) + 36.0 * info.n
+        else:
+            total += 4.0 * info.n * info.n + 8.0 * info.n
+    if H.levels == 1:
+        total += 4.0 * n * n
+    return total / n
 
 
 # ------------------------------------------------------------------------------
@@ -258,21 +293,31 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # Both precision strategies through the same pipeline (same kNN, locality order,
-    # row scaling, stopping test); the faster one is the headline value.
-    paths = {"fp32_refine": api.FP32_REFINE}
-    if not args.no_plain:
-        paths["fp64"] = api.FP64
+    # Precision strategies (FP32 inner + FP64 refinement, or plain FP64) times
+    # preconditioners (row abs-sum scaling, or one multigrid V-cycle), all through
+    # the same pipeline (same kNN, locality order, stopping test); the fastest is
+    # the headline value.
+    names = [p.strip() for p in args.paths.split(",") if p.strip()]
+    if args.no_plain:
+        names = [p for p in names if p.startswith("fp32_refine")]
     results = {}
     with ClockSampler(local) as clk:
-        for name, prec in paths.items():
-            pipe = Pipeline(n, k, 1, prec=prec, device=dev, precond=1, rtol=RTOL, stream=stream)
+        for name in names:
+            prec = api.FP32_REFINE if name.startswith("fp32_refine") else api.FP64
+            precond = 2 if name.endswith("+amg") else 1
+            pipe = Pipeline(n, k, 1, prec=prec, device=dev, precond=precond, rtol=RTOL, stream=stream)
             rec, _ = timed_runs(pipe, args.steps, args.warmup)
             info = pipe.decode()[0]
             u = pipe.u[:, 0].double().cpu().numpy()
             step_ms = [sum(r) for r in rec]
             results[name] = {"pipe": pipe, "rec": rec, "info": info, "u": u, "step_ms": step_ms,
-                             "ms": max_over_ranks(statistics.mean(step_ms))}
+                             "ms": max_over_ranks(statistics.mean(step_ms)), "mixed": prec == api.FP32_REFINE,
+                             "amg": precond == 2}
+            if precond == 2:
+                H = api.Hierarchy(n, k, 1.0, pipe.ws_amg, pipe.op)
+                results[name]["amg_coarse"] = amg_coarse_bytes(H, n)
+                results[name]["amg_levels"] = [int(H.info(lv).n) for lv in range(H.levels)]
+                results[name]["amg_width_max"] = int(H.info(0).width_max)
     clocks = clk.summary()
     best = min(results, key=lambda nm: results[nm]["ms"])
     R = results[best]
@@ -283,18 +328,24 @@ def main():
 
     # roofline of the dominant kernel: the persistent solver of the headline path
     solve_ms = statistics.mean(r[2] for r in rec)
-    mixed_best = best == "fp32_refine"
-    bytes_solve = solver_bytes_per_row(k, mixed_best, info[0], info[1]) * n
+    mixed_best = R["mixed"]
+    bytes_solve = solver_bytes_per_row(k, mixed_best, info[0], info[1], R.get("amg_coarse")) * n
     peak, peak_kind = measured_peaks()
     achieved = bytes_solve / (solve_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None,
-                "kernel": "k_solve (persistent BiCGSTAB, " + ("FP32 inner + FP64 refinement)" if mixed_best else "FP64)"),
-                "peak_kind": f"hbm_gbs of {peak_kind}", "bytes_per_launch": bytes_solve, "launch_ms": solve_ms}
+                "kernel": "k_solve (persistent BiCGSTAB, " + ("FP32 inner + FP64 refinement" if mixed_best else "FP64")
+                          + (", multigrid V-cycle preconditioner)" if R["amg"] else ", row scaling)"),
+                "peak_kind": f"hbm_gbs of {peak_kind}", "bytes_per_launch": bytes_solve, "launch_ms": solve_ms,
+                "note": "launch_ms is the solve stage: multigrid set-up (if any) + the persistent solver"}
 
     def summary(nm):
         r = results[nm]
-        return {"value": world * n / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "iters": r["info"][0],
+        extra = {}
+        if r["amg"]:
+            extra = {"amg_levels": r["amg_levels"], "amg_width_max": r["amg_width_max"],
+                     "amg_coarse_bytes_per_row": r["amg_coarse"]}
+        return {**extra, "value": world * n / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "iters": r["info"][0],
                 "outer": r["info"][1], "relres": r["info"][2], "status": r["info"][3],
                 "err_exact_inf": float(abs(r["u"] - pr.u_exact[:, 0]).max()),
                 "stage_ms": {"knn": statistics.mean(x[0] for x in r["rec"]),
@@ -305,7 +356,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if mixed_best else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "k": k, "rtol": RTOL, "precond": "row abs-sum scaling",
+        "config": {"workload": WORKLOAD, "n": n, "k": k, "rtol": RTOL,
+                   "precond": "multigrid V(1,1)-cycle (aggregation)" if R["amg"] else "row abs-sum scaling",
                    "path": best, "l2": "flushed before every step (256 MiB write), outside the step events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "p50_ms": statistics.median(step_ms),
@@ -319,10 +371,13 @@ def main():
         "paths": {nm: summary(nm) for nm in results},
     }
     if "fp64" in results:
-        a, b = results["fp32_refine"]["u"], results["fp64"]["u"]
-        line["paths"]["fp32_refine"]["solution_rel_diff_vs_fp64"] = float(
-            ((a - b) ** 2).sum() ** 0.5 / max((b ** 2).sum() ** 0.5, 1e-300))
-        line["speedup_fp32_refine_vs_plain_fp64"] = results["fp64"]["ms"] / results["fp32_refine"]["ms"]
+        b = results["fp64"]["u"]
+        for nm in results:
+            if nm != "fp64":
+                a = results[nm]["u"]
+                line["paths"][nm]["solution_rel_diff_vs_fp64"] = float(
+                    ((a - b) ** 2).sum() ** 0.5 / max((b ** 2).sum() ** 0.5, 1e-300))
+        line["speedup_vs_plain_fp64_rowscale"] = {nm: results["fp64"]["ms"] / results[nm]["ms"] for nm in results}
     mixed = R["pipe"]
 
     if not args.no_e2e:

@@ -213,7 +213,12 @@ typedef struct {
     int32_t precond;     /* 0 = none; 1 = left scaling of each row of the Krylov system by
                             1 / (|sigma| + sum_s |w_s|) (row equilibration: always positive,
                             unlike the Jacobi divisor sigma - w_self, which can vanish on rows
-                            of irregular samples that are not diagonally dominant) */
+                            of irregular samples that are not diagonally dominant);
+                            2 = right preconditioning by one aggregation-multigrid V-cycle
+                            (see mvgd_amg_setup) */
+    const void *amg;     /* precond == 2: the hierarchy from mvgd_amg_setup for this operator
+                            and sigma (DEVICE).  mvgd_solve builds one in its own workspace
+                            when this is NULL; mvgd_request_init requires it. */
 } mvgd_solve_opts;
 
 typedef struct {
@@ -224,10 +229,62 @@ typedef struct {
     int32_t reserved;
 } mvgd_solve_info;
 
-size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec);
+/* Workspace of mvgd_solve.  With precond == 2 it includes room for the
+ * hierarchy; a call given opts->amg needs that much less
+ * (mvgd_amg_workspace_bytes(n, k) rounded up to 256). */
+size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec, int32_t precond);
 mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const double *f, double *u,
                        const mvgd_solve_opts *opts, mvgd_solve_info *info, const int32_t *cancel,
                        void *workspace, size_t workspace_bytes, mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Aggregation multigrid.  The paper solves its systems with algebraic
+ * multigrid (Sec. 4.2, whose timing table grows about linearly in N)
+ * without naming a variant.  Here: plain aggregation on the stored row order
+ * (consecutive rows are spatial neighbours after the kNN step's cell sort).
+ *   - aggregate I of a level = its MVGD_AMG_AGG consecutive rows I*AGG ..;
+ *   - next level = Galerkin product P^T A P, P piecewise constant (FP64 sums,
+ *     kept as FP32 for the cycle);
+ *   - the first level with <= MVGD_AMG_COARSEST rows is inverted
+ *     (Gauss-Jordan with partial pivoting, FP32);
+ *   - one V(1,1)-cycle with l1-Jacobi smoothing, d_i = 1 / sum_j |a_ij|, in FP32.
+ * mvgd_amg_workspace_bytes: bytes of the hierarchy of an n-row operator with
+ *   K neighbours (0 if n or K is out of range).
+ * mvgd_amg_setup: builds the hierarchy of sigma I - L in amg_ws (DEVICE,
+ *   caller-owned, 256-byte aligned).  L must outlive it.  Asynchronous; what
+ *   only the device can find -- a coarse row wider than MVGD_AMG_MAX_WIDTH
+ *   (a row order that is not spatially coherent) or a singular coarsest
+ *   level -- is reported as MVGD_EDEGENERATE by mvgd_amg_describe.
+ * mvgd_amg_describe (synchronous): one level's size and DEVICE arrays, for
+ *   inspection.  Levels >= 1 are sliced like the operator (element (r, s) of
+ *   a width-w array at (r/32)*32*w + 32*s + r%32) with w = stride.
+ * mvgd_amg_apply: x = one V-cycle applied to b (FP64 [n][nrhs], DEVICE,
+ *   stored order); ws sized by mvgd_amg_apply_workspace_bytes.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+#define MVGD_AMG_AGG 8
+#define MVGD_AMG_COARSEST 512
+#define MVGD_AMG_MAX_WIDTH 64
+
+typedef struct {
+    int64_t n;             /* rows of this level */
+    int32_t levels;        /* levels in the hierarchy, the coarsest included */
+    int32_t stride;        /* slots per row: K + 1 at level 0, MVGD_AMG_MAX_WIDTH above */
+    int32_t status;        /* MVGD_OK or MVGD_EDEGENERATE (whole hierarchy) */
+    int32_t width_max;     /* widest coarse row found (whole hierarchy) */
+    const int32_t *col;    /* level 0: the operator's col; above: [n_pad][stride] columns */
+    const float *val;      /* FP32 values (level 0: the operator's weights, slot 0 = self) */
+    const double *val64;   /* levels >= 1: FP64 Galerkin sums */
+    const int32_t *cnt;    /* levels >= 1: entries of each row (sorted by column) */
+    const float *dinv;     /* [n] l1-Jacobi scaling */
+    const float *cinv;     /* coarsest level only: [n][n] row-major inverse */
+} mvgd_amg_info;
+
+size_t mvgd_amg_workspace_bytes(int64_t n, int32_t k);
+mvgd_status mvgd_amg_setup(const mvgd_ell *L, double sigma, void *amg_ws, size_t amg_bytes, mvgd_stream_t stream);
+mvgd_status mvgd_amg_describe(const void *amg_ws, int32_t level, mvgd_amg_info *out);
+size_t mvgd_amg_apply_workspace_bytes(int64_t n, int32_t nrhs);
+mvgd_status mvgd_amg_apply(const void *amg_ws, int64_t n, int32_t nrhs, const double *b, double *x, void *ws,
+                           size_t ws_bytes, mvgd_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Requests: the same solve (Sec. 4.2) split so that many systems advance in
@@ -241,10 +298,9 @@ mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const doub
  *
  * mvgd_request_init: gathers f (and u0, or zeros if u0 == NULL) into stored
  *   order and sets every right-hand side to its first restart.  Asynchronous.
- * mvgd_iterate: advances the listed requests (host array of request
- *   workspaces, with their row, RHS and neighbour counts K -- the K of the
- *   operator each was initialised with, 5..31, which sizes the launch's
- *   shared-memory staging; all of one precision) by at
+ * mvgd_iterate: advances the listed requests (host array of descriptors;
+ *   all of one precision and one preconditioner kind, the `precond` each was
+ *   initialised with) by at
  *   most max_iterations Krylov iterations in one cooperative launch; requests
  *   whose right-hand sides are all done cost nothing.  ctl_ws (size from
  *   mvgd_iterate_workspace_bytes for at least this many requests and rows)
@@ -254,20 +310,41 @@ mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const doub
  *   (DEVICE [nrhs]); a right-hand side not yet done reports MVGD_ENOCONV,
  *   or MVGD_ECANCELLED / MVGD_ETIMEOUT if a launch was cut short.
  * ------------------------------------------------------------------------ */
-size_t mvgd_request_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec);
+size_t mvgd_request_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec, int32_t precond);
 mvgd_status mvgd_request_init(void *req_workspace, size_t req_bytes, const mvgd_ell *L, int32_t nrhs,
                               double sigma, const double *f, const double *u0, const mvgd_solve_opts *opts,
                               mvgd_stream_t stream);
 size_t mvgd_iterate_workspace_bytes(int32_t max_requests, int64_t max_total_rows);
-mvgd_status mvgd_iterate(void *const *reqs, const int64_t *req_rows, const int32_t *req_nrhs,
-                         const int32_t *req_k, int32_t count, int32_t prec, int32_t max_iterations,
-                         const int32_t *cancel, void *ctl_workspace, size_t ctl_bytes, mvgd_stream_t stream);
+typedef struct {
+    void *workspace;  /* the request's workspace, as given to mvgd_request_init */
+    int64_t n;        /* rows of its operator */
+    int32_t nrhs;     /* its right-hand sides */
+    int32_t k;        /* K of its operator (sizes the launch's shared-memory staging) */
+} mvgd_request;
+mvgd_status mvgd_iterate(const mvgd_request *reqs, int32_t count, int32_t prec, int32_t precond,
+                         int32_t max_iterations, const int32_t *cancel, void *ctl_workspace, size_t ctl_bytes,
+                         mvgd_stream_t stream);
 mvgd_status mvgd_request_finish(void *req_workspace, int64_t n, int32_t nrhs, double *u,
                                 mvgd_solve_info *info, mvgd_stream_t stream);
 /* done (out, DEVICE int32 [count]): 1 where every right-hand side of the
  * request has finished (converged or stopped with a status), else 0.  A cheap
  * check between mvgd_iterate launches.  Asynchronous. */
 mvgd_status mvgd_request_poll(void *const *reqs, int32_t count, int32_t *done, mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Step trace (diagnostics; no counterpart in the paper).  When enabled, the
+ * persistent solver stamps the device clock (ns) after every grid-wide step:
+ * entry = code << 48 | (time & 2^48-1), code = Krylov phase 0..4 (PRE_A, A,
+ * PRE_B, B, C), or 0x100 | side << 8 | kind << 4 | level for a multigrid step
+ * (side 0: the cycle on p, 1: on s; kind 0 down, 1 coarsest, 2 up).  Process-
+ * wide, one device; entries past 65,536 wrap.  Both calls synchronise.
+ * mvgd_trace_enable: on != 0 clears the trace and turns it on for launches
+ *   made from now on; 0 turns it off.
+ * mvgd_trace_read: copies up to max entries to host memory; returns the count
+ *   (-1 on error).
+ * ------------------------------------------------------------------------ */
+mvgd_status mvgd_trace_enable(int32_t on);
+int32_t mvgd_trace_read(uint64_t *out, int32_t max);
 
 #ifdef __cplusplus
 }

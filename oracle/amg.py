@@ -1,7 +1,7 @@
 """Aggregation multigrid for (sigma I - L) -- TEST INFRASTRUCTURE ONLY (FP64).
 
-The paper solves its MVGD systems with algebraic multigrid (Sec. 4.2 and the
-timing discussion of Sec. 5) but does not say which variant.  The CUDA path
+The paper solves its MVGD systems with algebraic multigrid (Sec. 4.2, with its
+CPU-time table) but does not say which variant.  The CUDA path
 uses plain (unsmoothed) aggregation multigrid as a right preconditioner of
 BiCGSTAB; this module restates that preconditioner step by step from its
 definition, in FP64, so that the GPU hierarchy and V-cycle can be compared

@@ -24,7 +24,11 @@ EXPORTS = (
     "mvgd_assemble_workspace_bytes", "mvgd_assemble", "mvgd_spmv", "mvgd_solve_workspace_bytes", "mvgd_solve",
     "mvgd_request_workspace_bytes", "mvgd_request_init", "mvgd_iterate_workspace_bytes", "mvgd_iterate",
     "mvgd_request_finish", "mvgd_assemble_batch_workspace_bytes", "mvgd_assemble_batch", "mvgd_request_poll",
+    "mvgd_knn_noalloc", "mvgd_amg_workspace_bytes", "mvgd_amg_setup", "mvgd_amg_describe",
+    "mvgd_amg_apply_workspace_bytes", "mvgd_amg_apply", "mvgd_trace_enable", "mvgd_trace_read",
 )
+PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
+AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
 
 
 class DeltaRule(C.Structure):
@@ -38,12 +42,31 @@ class Ell(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("maxit", C.c_int32), ("inner_maxit", C.c_int32),
-                ("inner_rtol", C.c_double), ("max_outer", C.c_int32), ("precond", C.c_int32)]
+                ("inner_rtol", C.c_double), ("max_outer", C.c_int32), ("precond", C.c_int32), ("amg", _P)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int32), ("outer", C.c_int32), ("relres", C.c_double), ("status", C.c_int32),
                 ("reserved", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("workspace", _P), ("n", C.c_int64), ("nrhs", C.c_int32), ("k", C.c_int32)]
+
+
+def requests(items) -> C.Array:
+    """ctypes array of mvgd_request from (workspace tensor or pointer, n, nrhs, k) tuples."""
+    arr = (Request * len(items))()
+    for i, (ws, n, q, k) in enumerate(items):
+        ptr = ws if isinstance(ws, int) else ws.data_ptr()
+        arr[i] = Request(C.c_void_p(ptr), int(n), int(q), int(k))
+    return arr
+
+
+class AmgInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("stride", C.c_int32), ("status", C.c_int32),
+                ("width_max", C.c_int32), ("col", _P), ("val", _P), ("val64", _P), ("cnt", _P), ("dinv", _P),
+                ("cinv", _P)]
 
 
 class AssembleItem(C.Structure):
@@ -79,20 +102,20 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_assemble.restype = C.c_int
     L.mvgd_spmv.argtypes = [C.POINTER(Ell), C.c_int32, C.c_int32, C.c_double, C.c_double, _P, C.c_double, _P, _P]
     L.mvgd_spmv.restype = C.c_int
-    L.mvgd_solve_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32]
+    L.mvgd_solve_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     L.mvgd_solve_workspace_bytes.restype = C.c_size_t
     L.mvgd_solve.argtypes = [C.POINTER(Ell), C.c_int32, C.c_double, _P, _P, C.POINTER(SolveOpts), _P, _P, _P,
                              C.c_size_t, _P]
     L.mvgd_solve.restype = C.c_int
-    L.mvgd_request_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32]
+    L.mvgd_request_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
     L.mvgd_request_workspace_bytes.restype = C.c_size_t
     L.mvgd_request_init.argtypes = [_P, C.c_size_t, C.POINTER(Ell), C.c_int32, C.c_double, _P, _P,
                                     C.POINTER(SolveOpts), _P]
     L.mvgd_request_init.restype = C.c_int
     L.mvgd_iterate_workspace_bytes.argtypes = [C.c_int32, C.c_int64]
     L.mvgd_iterate_workspace_bytes.restype = C.c_size_t
-    L.mvgd_iterate.argtypes = [C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
-                               C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_size_t, _P]
+    L.mvgd_iterate.argtypes = [C.POINTER(Request), C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_size_t,
+                               _P]
     L.mvgd_iterate.restype = C.c_int
     L.mvgd_request_finish.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, _P]
     L.mvgd_request_finish.restype = C.c_int
@@ -104,6 +127,20 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_request_poll.restype = C.c_int
     L.mvgd_knn_noalloc.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, C.c_double, _P]
     L.mvgd_knn_noalloc.restype = C.c_int
+    L.mvgd_amg_workspace_bytes.argtypes = [C.c_int64, C.c_int32]
+    L.mvgd_amg_workspace_bytes.restype = C.c_size_t
+    L.mvgd_amg_setup.argtypes = [C.POINTER(Ell), C.c_double, _P, C.c_size_t, _P]
+    L.mvgd_amg_setup.restype = C.c_int
+    L.mvgd_amg_describe.argtypes = [_P, C.c_int32, C.POINTER(AmgInfo)]
+    L.mvgd_amg_describe.restype = C.c_int
+    L.mvgd_amg_apply_workspace_bytes.argtypes = [C.c_int64, C.c_int32]
+    L.mvgd_amg_apply_workspace_bytes.restype = C.c_size_t
+    L.mvgd_amg_apply.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, _P, C.c_size_t, _P]
+    L.mvgd_amg_apply.restype = C.c_int
+    L.mvgd_trace_enable.argtypes = [C.c_int32]
+    L.mvgd_trace_enable.restype = C.c_int
+    L.mvgd_trace_read.argtypes = [C.POINTER(C.c_uint64), C.c_int32]
+    L.mvgd_trace_read.restype = C.c_int32
     _lib = L
     return L
 

@@ -170,15 +170,25 @@ class SolveResult:
 def solve(op: Operator, f: torch.Tensor, *, u0: torch.Tensor | None = None, sigma: float = 1.0,
           rtol: float = 1e-8, maxit: int = 200000, inner_rtol: float = 1e-5, inner_maxit: int = 20000,
           max_outer: int = 60, precond: int = 0, cancel: torch.Tensor | None = None, stream=None,
-          workspace: torch.Tensor | None = None, sync: bool = True) -> SolveResult:
-    """Solve (sigma I - L) u = f; f, u FP64 [n] or [n][nrhs] in point order."""
+          workspace: torch.Tensor | None = None, sync: bool = True, amg: "Hierarchy | None" = None) -> SolveResult:
+    """Solve (sigma I - L) u = f; f, u FP64 [n] or [n][nrhs] in point order.
+
+    precond 2 preconditions with one multigrid V-cycle: pass a Hierarchy built
+    for this operator and sigma, or none to have the call build one."""
+    if amg is not None:
+        precond = LB.PRECOND_AMG
     _require_cuda(f, torch.float64, "f")
     nrhs = 1 if f.dim() == 1 else f.shape[1]
     u = torch.zeros_like(f) if u0 is None else u0.clone()
     L = LB.load()
-    need = L.mvgd_solve_workspace_bytes(op.n, op.k, nrhs, op.prec)
+    need = L.mvgd_solve_workspace_bytes(op.n, op.k, nrhs, op.prec, precond)
+    if need == 0:
+        raise ValueError("mvgd_solve_workspace_bytes: sizes out of range")
+    if amg is not None:  # the caller's hierarchy: no room needed for one
+        need -= (L.mvgd_amg_workspace_bytes(op.n, op.k) + 255) // 256 * 256
     ws = workspace if workspace is not None and workspace.numel() >= need else _workspace(need, f.device)
-    opts = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond)
+    opts = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond,
+                        _vp(amg.ws) if amg is not None else C.c_void_p(0))
     c = op.cstruct()
     if sync:
         info = (LB.SolveInfo * nrhs)()
@@ -199,3 +209,145 @@ def decode_info(dinfo: torch.Tensor) -> list:
     n = len(raw) // C.sizeof(LB.SolveInfo)
     arr = (LB.SolveInfo * n).from_buffer_copy(raw)
     return [(i.iters, i.outer, i.relres, i.status) for i in arr]
+
+
+@dataclass
+class Hierarchy:
+    """Aggregation-multigrid hierarchy of sigma I - L (mvgd_amg_setup)."""
+    n: int
+    k: int
+    sigma: float
+    ws: torch.Tensor
+    op: Operator
+
+    def info(self, level: int) -> LB.AmgInfo:
+        out = LB.AmgInfo()
+        LB.check("mvgd_amg_describe", LB.load().mvgd_amg_describe(_vp(self.ws), level, C.byref(out)))
+        return out
+
+    @property
+    def levels(self) -> int:
+        return self.info(0).levels
+
+    def level_rows(self, level: int):
+        """Host copies of one level (stored order): level 0 -> (dinv,); above ->
+        (cnt [n], col [n][stride], val64 [n][stride], val32 [n][stride], dinv [n])."""
+        i = self.info(level)
+        n = int(i.n)
+        npad = n_padded(n)
+        dev = self.ws.device
+
+        def grab(ptr, count, dtype):
+            return _device_view(ptr, count, dtype, dev).cpu().numpy()
+
+        dinv = grab(i.dinv, n, torch.float32)
+        if level == 0:
+            return (dinv,)
+        w = int(i.stride)
+        cnt = grab(i.cnt, n, torch.int32)
+        col = sell_to_rows(grab(i.col, npad * w, torch.int32), n, w)
+        v64 = sell_to_rows(grab(i.val64, npad * w, torch.float64), n, w)
+        v32 = sell_to_rows(grab(i.val, npad * w, torch.float32), n, w)
+        return cnt, col, v64, v32, dinv
+
+    def coarsest_inverse(self) -> np.ndarray:
+        i = self.info(self.levels - 1)
+        n = int(i.n)
+        return _device_view(i.cinv, n * n, torch.float32, self.ws.device).cpu().numpy().reshape(n, n)
+
+    def apply(self, b: torch.Tensor, stream=None) -> torch.Tensor:
+        """x = one V-cycle applied to b (FP64 [n] or [n][nrhs], stored order)."""
+        _require_cuda(b, torch.float64, "b")
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        L = LB.load()
+        x = torch.empty_like(b)
+        ws = _workspace(L.mvgd_amg_apply_workspace_bytes(self.n, nrhs), b.device)
+        LB.check("mvgd_amg_apply", L.mvgd_amg_apply(_vp(self.ws), self.n, nrhs, _vp(b), _vp(x), _vp(ws), ws.numel(),
+                                                     _stream(stream)))
+        return x
+
+
+class _DeviceArray:
+    """A raw device pointer seen through __cuda_array_interface__ (callers only read it)."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def _device_view(ptr, count: int, dtype, device) -> torch.Tensor:
+    typestr = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4"}[dtype]
+    p = ptr.value if hasattr(ptr, "value") else ptr
+    if not p:
+        raise ValueError("null device pointer")
+    return torch.as_tensor(_DeviceArray(p, count, typestr), device=device)
+
+
+def amg_setup(op: Operator, sigma: float = 1.0, stream=None) -> Hierarchy:
+    """Build the multigrid hierarchy of sigma I - L for operator op."""
+    L = LB.load()
+    nbytes = L.mvgd_amg_workspace_bytes(op.n, op.k)
+    if nbytes == 0:
+        raise ValueError("mvgd_amg_workspace_bytes: sizes out of range")
+    ws = _workspace(nbytes, op.col.device)
+    c = op.cstruct()
+    LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), float(sigma), _vp(ws), ws.numel(), _stream(stream)))
+    return Hierarchy(op.n, op.k, float(sigma), ws, op)
+
+
+def rows_to_sell(a: np.ndarray, w: int) -> np.ndarray:
+    """[n][w] rows -> sliced-ELL storage (slice height 32, slot-major inside a slice), zero padded."""
+    n = a.shape[0]
+    npad = n_padded(n)
+    full = np.zeros((npad, w), dtype=a.dtype)
+    full[:n] = a
+    return np.ascontiguousarray(full.reshape(npad // SLICE, SLICE, w).transpose(0, 2, 1)).ravel()
+
+
+def operator_from_rows(nbr: np.ndarray, val: np.ndarray, prec: int = FP64, device="cuda:0") -> Operator:
+    """An operator from host rows in their own order (no reordering): nbr [n][k]
+    int32, val [n][k+1] FP64 with slot 0 the row itself; FP32_REFINE splits each
+    weight into FP32 hi + lo."""
+    n, k = nbr.shape
+    col, v, lo = ell_alloc(n, k, prec, device)
+    c = rows_to_sell(np.ascontiguousarray(nbr, dtype=np.int32), k)
+    col[: c.size].copy_(torch.from_numpy(c))
+    if prec == FP64:
+        vv = rows_to_sell(np.asarray(val, dtype=np.float64), k + 1)
+        v[: vv.size].copy_(torch.from_numpy(vv))
+    else:
+        hi = np.asarray(val, dtype=np.float64).astype(np.float32)
+        rest = (np.asarray(val, dtype=np.float64) - hi.astype(np.float64)).astype(np.float32)
+        h = rows_to_sell(hi, k + 1)
+        r = rows_to_sell(rest, k + 1)
+        v[: h.size].copy_(torch.from_numpy(h))
+        lo[: r.size].copy_(torch.from_numpy(r))
+    return Operator(n, k, prec, col, v, lo, None)
+
+
+STEP_NAMES = {0: "PRE_A", 1: "A", 2: "PRE_B", 3: "B", 4: "C"}
+
+
+def trace_enable(on: bool = True) -> None:
+    """Turn the solver's step trace on (clearing it) or off."""
+    LB.check("mvgd_trace_enable", LB.load().mvgd_trace_enable(1 if on else 0))
+
+
+def trace_read(max_entries: int = 1 << 16) -> list:
+    """[(step name, ns since the previous step)] from the step trace."""
+    buf = (C.c_uint64 * max_entries)()
+    n = LB.load().mvgd_trace_read(buf, max_entries)
+    if n < 0:
+        raise MvgdError("mvgd_trace_read", LB.ECUDA)
+    out = []
+    prev = None
+    for i in range(n):
+        code, t = buf[i] >> 48, buf[i] & ((1 << 48) - 1)
+        if code >= 0x100:
+            side, kind, lvl = (code >> 8) & 1, (code >> 4) & 15, code & 15
+            name = f"V{'ps'[side]}:{('down', 'coarse', 'up')[kind]}{'' if kind == 1 else lvl}"
+        else:
+            name = STEP_NAMES.get(int(code), str(code))
+        out.append((name, None if prev is None else t - prev))
+        prev = t
+    return out

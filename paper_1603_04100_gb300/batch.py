@@ -36,6 +36,7 @@ class CloudSlot:
     req_ws: torch.Tensor
     u: torch.Tensor
     info: torch.Tensor
+    amg_ws: torch.Tensor | None = None
 
 
 class BatchPipeline:
@@ -54,10 +55,12 @@ class BatchPipeline:
             col, val, lo = api.ell_alloc(n, k, prec, dev)
             order = torch.empty(n, dtype=torch.int32, device=dev)
             op = api.Operator(n, k, prec, col, val, lo, order)
-            req = torch.empty(L.mvgd_request_workspace_bytes(n, k, q, prec), dtype=torch.uint8, device=dev)
+            req = torch.empty(L.mvgd_request_workspace_bytes(n, k, q, prec, precond), dtype=torch.uint8, device=dev)
+            amg = (torch.empty(L.mvgd_amg_workspace_bytes(n, k), dtype=torch.uint8, device=dev)
+                   if precond == LB.PRECOND_AMG else None)
             self.slots.append(CloudSlot(n, k, q, torch.empty((n, k), dtype=torch.int32, device=dev), order, op, req,
                                         torch.empty((n, q), dtype=torch.float64, device=dev),
-                                        torch.zeros(q * C.sizeof(LB.SolveInfo), dtype=torch.uint8, device=dev)))
+                                        torch.zeros(q * C.sizeof(LB.SolveInfo), dtype=torch.uint8, device=dev), amg))
         self.streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, n_streams))]
         nmax = max(n for n, _, _ in self.sizes)
         kmax = max(k for _, k, _ in self.sizes)
@@ -75,10 +78,14 @@ class BatchPipeline:
         self.cell_scale = cell_scale
         self.budget = maxit + 2 * (max_outer + 2) + 4
         cnt = len(self.slots)
-        self._reqs = (C.c_void_p * cnt)(*[s.req_ws.data_ptr() for s in self.slots])
-        self._rows = (C.c_int64 * cnt)(*[s.n for s in self.slots])
-        self._nrhs = (C.c_int32 * cnt)(*[s.nrhs for s in self.slots])
-        self._k = (C.c_int32 * cnt)(*[s.k for s in self.slots])
+        self.precond = precond
+        self._reqs = LB.requests([(s.req_ws, s.n, s.nrhs, s.k) for s in self.slots])
+        self._opts = []
+        for sl in self.slots:
+            o = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond)
+            if sl.amg_ws is not None:
+                o.amg = C.c_void_p(sl.amg_ws.data_ptr())
+            self._opts.append(o)
         self.graph = None
 
     @property
@@ -109,13 +116,14 @@ class BatchPipeline:
         s = api._stream(main)
         LB.check("mvgd_assemble_batch", L.mvgd_assemble_batch(items, len(self.slots), self.rule, vp(self.bad_rows),
                                                                vp(self.asm_ws), self.asm_ws.numel(), s))
-        for slot, f in zip(self.slots, f_list):
+        for slot, f, opts in zip(self.slots, f_list, self._opts):
             c = slot.op.cstruct()
+            if slot.amg_ws is not None:
+                LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(slot.amg_ws), slot.amg_ws.numel(), s))
             LB.check("mvgd_request_init", L.mvgd_request_init(vp(slot.req_ws), slot.req_ws.numel(), C.byref(c),
-                                                               slot.nrhs, 1.0, vp(f), None, C.byref(self.opts), s))
-        LB.check("mvgd_iterate", L.mvgd_iterate(self._reqs, self._rows, self._nrhs, self._k, len(self.slots),
-                                                 self.prec, self.budget, vp(cancel), vp(self.ctl_ws),
-                                                 self.ctl_ws.numel(), s))
+                                                               slot.nrhs, 1.0, vp(f), None, C.byref(opts), s))
+        LB.check("mvgd_iterate", L.mvgd_iterate(self._reqs, len(self.slots), self.prec, self.precond, self.budget,
+                                                 vp(cancel), vp(self.ctl_ws), self.ctl_ws.numel(), s))
         for slot in self.slots:
             LB.check("mvgd_request_finish", L.mvgd_request_finish(vp(slot.req_ws), slot.n, slot.nrhs, vp(slot.u),
                                                                    vp(slot.info), s))

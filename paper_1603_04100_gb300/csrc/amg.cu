@@ -1,0 +1,479 @@
+// Aggregation multigrid hierarchy of sigma I - L and its standalone V-cycle.
+//
+// The paper solves its MVGD systems with algebraic multigrid and reports its
+// CPU time growing about linearly with N (Sec. 4.2, the timing table), without
+// naming the variant.  This is plain aggregation (Braess 1995) on the
+// stored row order, whose consecutive rows are spatial neighbours (the kNN
+// step sorts points by cell along a Z-order curve):
+//   * aggregate I of level l is rows kAmgAgg*I .. kAmgAgg*I + kAmgAgg-1;
+//   * level l+1 is the Galerkin product P^T A_l P (entry (I, J) sums a_ij over
+//     the rows of aggregate I and the columns of aggregate J), computed in
+//     FP64 one warp per coarse row, with a fixed summation order;
+//   * the first level with at most kAmgCoarsest rows is inverted by
+//     Gauss-Jordan elimination with partial pivoting (FP32, one block);
+//   * smoothing is l1-Jacobi (Baker, Falgout, Kolev, Yang 2011): d_i =
+//     1 / sum_j |a_ij|, positive on every row whatever the sign pattern.
+// Everything the V-cycle reads is FP32; the FP64 Galerkin values stay
+// available for inspection.
+#include <limits.h>
+#include <string.h>
+
+#include "vcycle.cuh"
+
+namespace mvgd {
+namespace {
+
+struct AmgLayout {
+    AmgHeader* hdr;
+    AmgHeader h;  // host copy of the pointers and sizes
+};
+
+AmgLayout amg_layout(void* ws, int64_t n, int k) {
+    AmgLayout A;
+    memset(&A.h, 0, sizeof(A.h));
+    Carver cv(ws);
+    A.hdr = cv.take<AmgHeader>(1);
+    int64_t sizes[kAmgMaxLevels];
+    const int nlev = amg_levels(n, sizes);
+    A.h.nlev = nlev;
+    A.h.k = k;
+    A.h.n = n;
+    for (int l = 0; l < nlev; l++) {
+        const int64_t nl = sizes[l], np = n_padded(nl);
+        AmgLevel& L = A.h.lv[l];
+        L.n = nl;
+        if (l == 0) {
+            L.val = cv.take<float>(np * (k + 1));
+        } else {
+            L.col = cv.take<int32_t>(np * kAmgStride);
+            L.val = cv.take<float>(np * kAmgStride);
+            L.val64 = cv.take<double>(np * kAmgStride);
+            L.cnt = cv.take<int32_t>(np);
+            L.sw = cv.take<int32_t>(np / kSlice);
+        }
+        L.dinv = cv.take<float>(np);
+    }
+    const int64_t nc = nlev > 0 ? sizes[nlev - 1] : 0;
+    A.h.nc = nc;
+    A.h.dense = cv.take<float>(nc * nc);
+    A.h.cinv = cv.take<float>(nc * nc);
+    A.h.piv = cv.take<int32_t>(nc);
+    A.h.bytes = cv.used;
+    return A;
+}
+
+// Where the set-up reads the operator's own weights (FP64, or hi + lo).
+struct OpView {
+    const int32_t* col;
+    const void* val;
+    const float* val_lo;
+    int prec;
+};
+
+__device__ __forceinline__ double op_weight(const OpView& O, int64_t idx) {
+    return O.prec == MVGD_FP64 ? static_cast<const double*>(O.val)[idx]
+                               : (double)static_cast<const float*>(O.val)[idx] + (double)O.val_lo[idx];
+}
+
+__global__ void k_amg_header(AmgHeader h, AmgHeader* dst) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = h;
+}
+
+// Level 0: FP32 copy of the weights and the l1 scaling of sigma I - L.
+__global__ void k_amg_level0(const AmgHeader* __restrict__ Hp, OpView O) {
+    const AmgHeader& H = *Hp;
+    const int k = H.k, m = k + 1;
+    const double sigma = H.sigma;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < H.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
+        double l1 = 0.0;
+        for (int s = 0; s < m; s++) {
+            const double w = op_weight(O, vb + (int64_t)s * kSlice);
+            H.lv[0].val[vb + (int64_t)s * kSlice] = (float)w;
+            l1 += s == 0 ? fabs(sigma - w) : fabs(w);
+        }
+        H.lv[0].dinv[r] = l1 > 0.0 ? (float)(1.0 / l1) : 1.0f;
+    }
+}
+
+constexpr int kPerLane = kAmgAgg * kAmgStride / kWarp;  // entries a lane holds while coarsening
+
+// Level l+1 from level l, one warp per coarse row I: gather the entries of
+// the aggregate's rows, then emit distinct aggregate columns in increasing
+// order, each with the FP64 sum of its entries (per-lane sums in entry order,
+// then a butterfly over the warp: the same order on every run).
+__global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
+    const AmgHeader& H = *Hp;
+    const AmgLevel& F = H.lv[l];
+    const AmgLevel& Cl = H.lv[l + 1];
+    const int lane = (int)lane_id();
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x / kWarp);
+    const int k = H.k;
+    const int W = (l == 0) ? k + 1 : kAmgStride;  // entry slots per fine row
+    for (int64_t I = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp; I < Cl.n; I += warps) {
+        int key[kPerLane];
+        double v[kPerLane];
+#pragma unroll
+        for (int t = 0; t < kPerLane; t++) {
+            key[t] = INT_MAX;
+            v[t] = 0.0;
+            const int e = t * kWarp + lane;
+            const int f = e / W, s = e % W;
+            const int64_t i = I * kAmgAgg + f;
+            if (f >= kAmgAgg || i >= F.n) continue;
+            if (l == 0) {
+                const int64_t vb = (i / kSlice) * (int64_t)(kSlice * (k + 1)) + (i % kSlice);
+                const double w = op_weight(O, vb + (int64_t)s * kSlice);
+                if (s == 0) {
+                    key[t] = (int)(i / kAmgAgg);
+                    v[t] = H.sigma - w;
+                } else {
+                    const int64_t j = O.col[(i / kSlice) * (int64_t)(kSlice * k) + (int64_t)(s - 1) * kSlice + (i % kSlice)];
+                    key[t] = (int)(j / kAmgAgg);
+                    v[t] = -w;
+                }
+            } else if (s < F.cnt[i]) {
+                const int64_t idx = (i / kSlice) * (int64_t)(kSlice * kAmgStride) + (int64_t)s * kSlice + (i % kSlice);
+                key[t] = F.col[idx] / kAmgAgg;
+                v[t] = F.val64[idx];
+            }
+        }
+        const int64_t ob = (I / kSlice) * (int64_t)(kSlice * kAmgStride) + (I % kSlice);
+        int out = 0;
+        double l1 = 0.0;
+        while (true) {
+            int mine = INT_MAX;
+#pragma unroll
+            for (int t = 0; t < kPerLane; t++) mine = min(mine, key[t]);
+            int m = mine;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (m == INT_MAX) break;
+            double part = 0.0;
+#pragma unroll
+            for (int t = 0; t < kPerLane; t++)
+                if (key[t] == m) {
+                    part += v[t];
+                    key[t] = INT_MAX;
+                }
+            const double tot = warp_sum(part);
+            if (out < kAmgStride && lane == 0) {
+                Cl.col[ob + (int64_t)out * kSlice] = m;
+                Cl.val64[ob + (int64_t)out * kSlice] = tot;
+                Cl.val[ob + (int64_t)out * kSlice] = (float)tot;
+            }
+            l1 += fabs(tot);
+            out++;
+        }
+        if (lane == 0) {
+            if (out > kAmgStride) atomicCAS((int*)&Hp->status, 0, (int)MVGD_EDEGENERATE);
+            atomicMax((int*)&Hp->width_max, out);
+            const int c = min(out, kAmgStride);
+            Cl.cnt[I] = c;
+            Cl.dinv[I] = l1 > 0.0 ? (float)(1.0 / l1) : 1.0f;
+        }
+        // padding: (own row, 0) up to the full stride, so slice loops need no bounds
+        for (int s = min(out, kAmgStride) + lane; s < kAmgStride; s += kWarp) {
+            Cl.col[ob + (int64_t)s * kSlice] = (int32_t)I;
+            Cl.val64[ob + (int64_t)s * kSlice] = 0.0;
+            Cl.val[ob + (int64_t)s * kSlice] = 0.0f;
+        }
+    }
+}
+
+// Widest row of each 32-row slice of level l (>= 1).
+__global__ void k_amg_slice_width(const AmgHeader* __restrict__ Hp, int l) {
+    const AmgLevel& L = Hp->lv[l];
+    const int64_t ns = (L.n + kSlice - 1) / kSlice;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns; s += (int64_t)gridDim.x * blockDim.x) {
+        int w = 0;
+        for (int64_t r = s * kSlice; r < (s + 1) * kSlice && r < L.n; r++) w = max(w, L.cnt[r]);
+        L.sw[s] = w;
+    }
+}
+
+// The coarsest level as a dense FP32 matrix (zeroed first).
+__global__ void k_amg_dense(const AmgHeader* __restrict__ Hp, OpView O) {
+    const AmgHeader& H = *Hp;
+    const int m = H.nlev - 1;
+    const int64_t nc = H.nc;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nc; r += (int64_t)gridDim.x * blockDim.x) {
+        float* row = H.dense + r * nc;
+        if (m == 0) {
+            const int k = H.k;
+            const int64_t vb = (r / kSlice) * (int64_t)(kSlice * (k + 1)) + (r % kSlice);
+            row[r] = (float)(H.sigma - op_weight(O, vb));
+            for (int s = 0; s < k; s++) {
+                const int64_t j = O.col[(r / kSlice) * (int64_t)(kSlice * k) + (int64_t)s * kSlice + (r % kSlice)];
+                row[j] = (float)(-op_weight(O, vb + (int64_t)(s + 1) * kSlice));
+            }
+        } else {
+            const AmgLevel& L = H.lv[m];
+            const int64_t b = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
+            for (int s = 0; s < L.cnt[r]; s++) row[L.col[b + (int64_t)s * kSlice]] = L.val[b + (int64_t)s * kSlice];
+        }
+    }
+}
+
+// Gauss-Jordan inversion in place with partial pivoting, one block.  Step k
+// picks the largest |a_ik|, i >= k (lowest i on ties), swaps rows k and p,
+// and replaces a by the matrix of the eliminated system; the column swaps
+// are undone in reverse order at the end (the classical in-place form).
+constexpr int kInvThreads = 1024;
+__global__ void __launch_bounds__(kInvThreads) k_amg_invert(AmgHeader* Hp) {
+    const int64_t n = Hp->nc;
+    float* a = Hp->dense;
+    int32_t* piv = Hp->piv;
+    __shared__ float colk[kAmgCoarsest];
+    __shared__ float rowk[kAmgCoarsest];
+    __shared__ float bv[kInvThreads / 32];
+    __shared__ int bi[kInvThreads / 32];
+    __shared__ int bad;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) bad = 0;
+    __syncthreads();
+    for (int64_t k = 0; k < n; k++) {
+        // pivot search
+        float best = -1.0f;
+        int bidx = INT_MAX;
+        for (int64_t i = k + tid; i < n; i += kInvThreads) {
+            const float v = fabsf(a[i * n + k]);
+            if (v > best) { best = v; bidx = (int)i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+            if (ov > best || (ov == best && oi < bidx)) { best = ov; bidx = oi; }
+        }
+        if (lane == 0) { bv[wid] = best; bi[wid] = bidx; }
+        __syncthreads();
+        if (tid == 0) {
+            float b = -1.0f;
+            int p = INT_MAX;
+            for (int w = 0; w < kInvThreads / 32; w++)
+                if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
+            if (!(b > 0.0f) || !isfinite(b)) bad = 1;
+            piv[k] = p == INT_MAX ? (int)k : p;
+        }
+        __syncthreads();
+        if (bad) break;
+        const int64_t p = piv[k];
+        if (p != k)
+            for (int64_t j = tid; j < n; j += kInvThreads) {
+                const float t = a[k * n + j];
+                a[k * n + j] = a[p * n + j];
+                a[p * n + j] = t;
+            }
+        __syncthreads();
+        const float inv = 1.0f / a[k * n + k];
+        for (int64_t i = tid; i < n; i += kInvThreads) {
+            colk[i] = a[i * n + k];
+            rowk[i] = (i == k) ? inv : a[k * n + i] * inv;
+        }
+        __syncthreads();
+        for (int64_t e = tid; e < n * n; e += kInvThreads) {
+            const int64_t i = e / n, j = e % n;
+            if (i == k) {
+                a[e] = rowk[j];
+            } else if (j == k) {
+                a[e] = -colk[i] * inv;
+            } else {
+                a[e] = fmaf(-colk[i], rowk[j], a[e]);
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        if (tid == 0) atomicCAS((int*)&Hp->status, 0, (int)MVGD_EDEGENERATE);
+        return;
+    }
+    // undo the column interchanges, last first
+    for (int64_t k = n - 1; k >= 0; k--) {
+        const int64_t p = piv[k];
+        if (p != k)
+            for (int64_t i = tid; i < n; i += kInvThreads) {
+                const float t = a[i * n + k];
+                a[i * n + k] = a[i * n + p];
+                a[i * n + p] = t;
+            }
+        __syncthreads();
+    }
+    for (int64_t e = tid; e < n * n; e += kInvThreads) Hp->cinv[e] = a[e];
+}
+
+int grid_for(int64_t threads) {
+    int64_t g = (threads + 255) / 256;
+    return (int)(g > 16384 ? 16384 : (g < 1 ? 1 : g));
+}
+
+// ---------------------------------------------------------------------------
+// Standalone V-cycle (stored order): one kernel per step.
+// ---------------------------------------------------------------------------
+struct ApplyVecs {
+    float* y[kAmgMaxLevels];
+    float* r[kAmgMaxLevels];
+    float* b[kAmgMaxLevels];  // b[0] unused: level 0 reads the FP64 input
+    float* x[kAmgMaxLevels];  // x[0] unused: level 0 writes the FP64 output
+    size_t bytes;
+};
+
+ApplyVecs apply_layout(void* ws, int64_t n, int Q) {
+    ApplyVecs V;
+    memset(&V, 0, sizeof(V));
+    int64_t sizes[kAmgMaxLevels];
+    const int nlev = amg_levels(n, sizes);
+    Carver cv(ws);
+    for (int l = 0; l < nlev; l++) {
+        const int64_t m = n_padded(sizes[l]) * Q;
+        V.y[l] = cv.take<float>(m);
+        V.r[l] = cv.take<float>(m);
+        if (l > 0) {
+            V.b[l] = cv.take<float>(m);
+            V.x[l] = cv.take<float>(m);
+        }
+    }
+    V.bytes = cv.used;
+    return V;
+}
+
+// Rows of a level in whole warps: rows past the end only join the shuffles.
+__global__ void k_vpre(const AmgHeader* __restrict__ Hp, const double* __restrict__ b, int Q, float* y0) {
+    const AmgHeader& H = *Hp;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < H.n * Q; e += (int64_t)gridDim.x * blockDim.x)
+        y0[e] = H.lv[0].dinv[e / Q] * (float)b[e];
+}
+
+__global__ void k_vdown(const AmgHeader* __restrict__ Hp, int l, const double* __restrict__ b0, int Q, ApplyVecs V) {
+    const AmgHeader& H = *Hp;
+    const int64_t nl = H.lv[l].n;
+    const float* Y = V.y[l];
+    const bool last = (l + 1 == H.nlev - 1);
+    // the stride is a multiple of 32, so each warp stays on 32 consecutive rows
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n_padded(nl);
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const bool valid = r < nl;
+        for (int q = 0; q < Q; q++) {
+            const float bi = valid ? (l == 0 ? (float)b0[r * Q + q] : V.b[l][r * Q + q]) : 0.0f;
+            const float yi = valid ? Y[r * Q + q] : 0.0f;
+            vdown_row(H, l, r, valid, Q, q, bi, yi, [&](int64_t j) { return Y[j * Q + q]; }, V.r[l], V.b[l + 1],
+                      last ? nullptr : V.y[l + 1]);
+        }
+    }
+}
+
+__global__ void k_vcoarse(const AmgHeader* __restrict__ Hp, const double* __restrict__ b0, double* x0, int Q,
+                          ApplyVecs V) {
+    const AmgHeader& H = *Hp;
+    const int m = H.nlev - 1;
+    const int64_t rho = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kWarp;
+    if (rho >= H.nc) return;  // warp-uniform
+    for (int q = 0; q < Q; q++) {
+        float x;
+        if (m == 0) x = coarse_row(H, rho, [&](int64_t c) { return (float)b0[c * Q + q]; });
+        else x = coarse_row(H, rho, [&](int64_t c) { return V.b[m][c * Q + q]; });
+        if (lane_id() == 0) {
+            if (m == 0) x0[rho * Q + q] = (double)x;
+            else V.x[m][rho * Q + q] = x;
+        }
+    }
+}
+
+__global__ void k_vup(const AmgHeader* __restrict__ Hp, int l, double* x0, int Q, ApplyVecs V) {
+    const AmgHeader& H = *Hp;
+    const int64_t nl = H.lv[l].n;
+    const float* Xc = V.x[l + 1];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nl; r += (int64_t)gridDim.x * blockDim.x) {
+        for (int q = 0; q < Q; q++) {
+            const float x = vup_row(H, l, r, Q, q, V.y[l][r * Q + q], V.r[l][r * Q + q],
+                                    [&](int64_t J) { return Xc[J * Q + q]; });
+            if (l == 0) x0[r * Q + q] = (double)x;
+            else V.x[l][r * Q + q] = x;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace mvgd
+
+using namespace mvgd;
+
+MVGD_API size_t mvgd_amg_workspace_bytes(int64_t n, int32_t k) {
+    if (n < 1 || k < kMinK || k > kMaxK || amg_levels(n, nullptr) == 0) return 0;
+    return amg_layout(nullptr, n, k).h.bytes;
+}
+
+MVGD_API mvgd_status mvgd_amg_setup(const mvgd_ell* L, double sigma, void* amg_ws, size_t amg_bytes,
+                                    mvgd_stream_t stream) {
+    if (!L || !amg_ws || !L->col || !L->val || L->n < 2 || L->n >= (1ll << 31) || L->k < kMinK || L->k > kMaxK)
+        return MVGD_EINVAL;
+    if (L->prec != MVGD_FP64 && L->prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    if (L->prec == MVGD_FP32_REFINE && !L->val_lo) return MVGD_EINVAL;
+    if (!aligned(amg_ws) || !aligned(L->col) || !aligned(L->val) || !aligned(L->val_lo)) return MVGD_EINVAL;
+    if (!(sigma == sigma)) return MVGD_EINVAL;
+    if (amg_levels(L->n, nullptr) == 0) return MVGD_EINVAL;
+    AmgLayout A = amg_layout(amg_ws, L->n, L->k);
+    if (amg_bytes < A.h.bytes) return MVGD_EWORKSPACE;
+    A.h.sigma = sigma;
+    A.h.col0 = L->col;
+    A.h.status = MVGD_OK;
+    A.h.width_max = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    OpView O{L->col, L->val, L->val_lo, L->prec};
+    k_amg_header<<<1, 1, 0, s>>>(A.h, A.hdr);
+    k_amg_level0<<<grid_for(L->n), 256, 0, s>>>(A.hdr, O);
+    for (int l = 0; l + 1 < A.h.nlev; l++) {
+        const int64_t nc = A.h.lv[l + 1].n;
+        k_amg_coarsen<<<grid_for(nc * kWarp), 256, 0, s>>>(A.hdr, O, l);
+        k_amg_slice_width<<<grid_for(nc / kSlice + 1), 256, 0, s>>>(A.hdr, l + 1);
+    }
+    MVGD_CUDA_TRY(cudaMemsetAsync(A.h.dense, 0, sizeof(float) * A.h.nc * A.h.nc, s));
+    k_amg_dense<<<grid_for(A.h.nc), 256, 0, s>>>(A.hdr, O);
+    k_amg_invert<<<1, kInvThreads, 0, s>>>(A.hdr);
+    return launch_status();
+}
+
+MVGD_API mvgd_status mvgd_amg_describe(const void* amg_ws, int32_t level, mvgd_amg_info* out) {
+    if (!amg_ws || !out || !aligned(amg_ws)) return MVGD_EINVAL;
+    AmgHeader h;
+    MVGD_CUDA_TRY(cudaMemcpy(&h, amg_ws, sizeof(h), cudaMemcpyDeviceToHost));
+    if (level < 0 || level >= h.nlev) return MVGD_EINVAL;
+    const AmgLevel& L = h.lv[level];
+    memset(out, 0, sizeof(*out));
+    out->levels = h.nlev;
+    out->status = h.status;
+    out->width_max = h.width_max;
+    out->n = L.n;
+    out->stride = level == 0 ? h.k + 1 : kAmgStride;
+    out->col = level == 0 ? h.col0 : L.col;
+    out->val = L.val;
+    out->val64 = L.val64;
+    out->cnt = L.cnt;
+    out->dinv = L.dinv;
+    out->cinv = level == h.nlev - 1 ? h.cinv : nullptr;
+    return MVGD_OK;
+}
+
+MVGD_API size_t mvgd_amg_apply_workspace_bytes(int64_t n, int32_t nrhs) {
+    if (n < 1 || nrhs < 1 || nrhs > 8 || amg_levels(n, nullptr) == 0) return 0;
+    return apply_layout(nullptr, n, nrhs).bytes;
+}
+
+MVGD_API mvgd_status mvgd_amg_apply(const void* amg_ws, int64_t n, int32_t nrhs, const double* b, double* x,
+                                    void* ws, size_t ws_bytes, mvgd_stream_t stream) {
+    if (!amg_ws || !b || !x || !ws || n < 1 || nrhs < 1 || nrhs > 8) return MVGD_EINVAL;
+    if (!aligned(amg_ws) || !aligned(b) || !aligned(x) || !aligned(ws)) return MVGD_EINVAL;
+    int64_t sizes[kAmgMaxLevels];
+    const int nlev = amg_levels(n, sizes);
+    if (nlev == 0) return MVGD_EINVAL;
+    ApplyVecs V = apply_layout(ws, n, nrhs);
+    if (ws_bytes < V.bytes) return MVGD_EWORKSPACE;
+    const AmgHeader* H = static_cast<const AmgHeader*>(amg_ws);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int m = nlev - 1;
+    if (m > 0) k_vpre<<<grid_for(n * nrhs), 256, 0, s>>>(H, b, nrhs, V.y[0]);
+    for (int l = 0; l < m; l++) k_vdown<<<grid_for(n_padded(sizes[l])), 256, 0, s>>>(H, l, b, nrhs, V);
+    k_vcoarse<<<grid_for(sizes[m] * kWarp), 256, 0, s>>>(H, b, x, nrhs, V);
+    for (int l = m - 1; l >= 0; l--) k_vup<<<grid_for(sizes[l]), 256, 0, s>>>(H, l, x, nrhs, V);
+    return launch_status();
+}

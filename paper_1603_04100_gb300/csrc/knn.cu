@@ -341,6 +341,101 @@ __global__ void k_sort_buckets(const int* __restrict__ start, int nbuckets, floa
 }
 
 // ---------------------------------------------------------------------------
+// The row order exported to callers: every point along one Z-order curve of
+// the bounding cube (21 bits per axis), ties by index.  Consecutive points of
+// this order are spatial neighbours at every scale down to a few points --
+// which the kNN's hashed cell buckets are not where the hash wraps around the
+// grid -- and aggregation multigrid, which groups consecutive rows, relies on
+// it.  A stable LSD radix sort of (key, index) pairs, 8 bits per pass.
+// ---------------------------------------------------------------------------
+constexpr int kRadixThreads = 256;
+constexpr int kRadixTile = 4096;  // elements per block: 16 rounds of 256
+constexpr int kRadixWarps = kRadixThreads / 32;
+
+__device__ __forceinline__ uint64_t spread3_21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void k_zorder_keys(const double* __restrict__ pts, int64_t n, const KnnParams* __restrict__ P,
+                              uint64_t* __restrict__ key, int* __restrict__ val) {
+    const KnnParams p = *P;
+    const double e = fmax(p.ext[0], fmax(p.ext[1], p.ext[2]));
+    const double scale = e > 0.0 ? 2097152.0 / e : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            double t = (pts[3 * i + a] - p.lo[a]) * scale;
+            t = t < 0.0 ? 0.0 : (t > 2097151.0 ? 2097151.0 : t);
+            k |= spread3_21((uint32_t)t) << a;
+        }
+        key[i] = k;
+        val[i] = (int)i;
+    }
+}
+
+// Digit histogram of each tile, stored digit-major: counts[digit * nblocks + block].
+__global__ void __launch_bounds__(kRadixThreads) k_radix_count(const uint64_t* __restrict__ key, int64_t n, int shift,
+                                                               int* __restrict__ counts) {
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    const int64_t end = base + kRadixTile < n ? base + kRadixTile : n;
+    for (int64_t i = base + threadIdx.x; i < end; i += kRadixThreads) atomicAdd(&h[(key[i] >> shift) & 255u], 1);
+    __syncthreads();
+    counts[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter: the tile is read in order (round by round, thread by thread),
+// and each element goes after every earlier element of its digit.
+__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint64_t* __restrict__ kin,
+                                                                 const int* __restrict__ vin, int64_t n, int shift,
+                                                                 const int* __restrict__ offs,
+                                                                 uint64_t* __restrict__ kout, int* __restrict__ vout) {
+    __shared__ int run[256];
+    __shared__ int wcnt[kRadixWarps][256];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    run[tid] = offs[tid * gridDim.x + blockIdx.x];
+    for (int w = 0; w < kRadixWarps; w++) wcnt[w][tid] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kRadixTile;
+    for (int round = 0; round < kRadixTile / kRadixThreads; round++) {
+        const int64_t i = base + (int64_t)round * kRadixThreads + tid;
+        const bool valid = i < n;
+        const uint64_t k = valid ? kin[i] : 0;
+        const int v = valid ? vin[i] : 0;
+        const unsigned d = valid ? (unsigned)((k >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[wid][d] = __popc(peers);
+        __syncthreads();
+        int tot = 0;
+        for (int w = 0; w < kRadixWarps; w++) {  // exclusive prefix over warps, digit tid
+            const int c = wcnt[w][tid];
+            wcnt[w][tid] = tot;
+            tot += c;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = run[d] + wcnt[wid][d] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+        run[tid] += tot;
+        for (int w = 0; w < kRadixWarps; w++) wcnt[w][tid] = 0;
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Query
 // ---------------------------------------------------------------------------
 struct AxisRange {
@@ -510,6 +605,10 @@ struct KnnLayout {
     uint32_t* pcell;  // [n][3]
     float4* sorted;
     int* order;
+    uint64_t* zkey[2];  // radix-sort buffers of the exported order
+    int* zval[2];
+    int* zcount;        // [256 * radix blocks + 1]
+    int* zsums;
     size_t bytes;
     int nbuckets_max;
 };
@@ -535,6 +634,13 @@ KnnLayout knn_layout(void* ws, int64_t n) {
     L.pcell = cv.take<uint32_t>(3 * n);
     L.sorted = cv.take<float4>(n);
     L.order = cv.take<int>(n);
+    const int64_t rblocks = (n + kRadixTile - 1) / kRadixTile;
+    for (int b = 0; b < 2; b++) {
+        L.zkey[b] = cv.take<uint64_t>(n);
+        L.zval[b] = cv.take<int>(n);
+    }
+    L.zcount = cv.take<int>(256 * rblocks + 1);
+    L.zsums = cv.take<int>((256 * rblocks + kScanTile - 1) / kScanTile + 1);
     L.bytes = cv.used;
     return L;
 }
@@ -588,7 +694,22 @@ MVGD_API mvgd_status mvgd_knn(const double* pts, int64_t n, int32_t k, int32_t* 
     if (qblocks > sms * 16) qblocks = sms * 16;
     k_query<<<qblocks, kQueryWarps * 32, 0, s>>>(pts, n, k, L.params, L.sorted, L.start, L.order,
                                                  L.pcell, nbr);
-    if (order) MVGD_CUDA_TRY(cudaMemcpyAsync(order, L.order, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    if (order) {
+        const int rblocks = (int)((n + kRadixTile - 1) / kRadixTile);
+        const int len = 256 * rblocks;
+        const int st = (len + kScanTile - 1) / kScanTile;
+        k_zorder_keys<<<gb, tb, 0, s>>>(pts, n, L.params, L.zkey[0], L.zval[0]);
+        for (int pass = 0; pass < 8; pass++) {
+            const int a = pass & 1;
+            k_radix_count<<<rblocks, kRadixThreads, 0, s>>>(L.zkey[a], n, 8 * pass, L.zcount);
+            k_scan_tiles<<<st, 1024, 0, s>>>(L.zcount, len, L.zsums);
+            k_scan_sums<<<1, 32, 0, s>>>(L.zsums, st);
+            k_scan_add<<<st, 1024, 0, s>>>(L.zcount, len, L.zsums, len, n);
+            k_radix_scatter<<<rblocks, kRadixThreads, 0, s>>>(L.zkey[a], L.zval[a], n, 8 * pass, L.zcount,
+                                                              L.zkey[a ^ 1], L.zval[a ^ 1]);
+        }
+        MVGD_CUDA_TRY(cudaMemcpyAsync(order, L.zval[0], sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+    }
     return launch_status();
 }
 
@@ -617,7 +738,7 @@ MVGD_API mvgd_status mvgd_knn(const double* pts, int64_t n, int32_t k, int32_t* 
 namespace mvgd {
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;  // >= knn workspace of 65,536 points
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // >= knn workspace of 65,536 points
 static __device__ __align__(256) unsigned char g_knn_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;

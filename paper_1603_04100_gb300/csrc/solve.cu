@@ -28,9 +28,11 @@
 //   INNER    BiCGSTAB until the recursive residual meets the restart target;
 //            a diverging FP32 inner solve is abandoned and its correction dropped
 //   DONE
+#include <string.h>
+
 #include <type_traits>
 
-#include "common.cuh"
+#include "vcycle.cuh"
 
 namespace mvgd {
 namespace {
@@ -55,7 +57,7 @@ struct RhsState {
     int best_flag;   // the last iteration reached a new smallest inner residual: copy x to x_best
     int fold_best;   // on restart, fold x_best (not x) into u
     int since_best;  // inner iterations since the smallest residual last dropped by 1%
-    int pad1;
+    int pending;     // multigrid flow: the last step's x += alpha ph + omega sh is still to apply
 };
 
 // One request: an operator, its right-hand sides and all solver state.
@@ -83,6 +85,15 @@ struct Prob {
     double* part;      // [kRedSlots][kChan][nchunk][Q]
     unsigned* arrive;  // [kRedSlots]
     int nchunk, pad;
+    // multigrid right preconditioning (precond == 2); amg == nullptr otherwise
+    const AmgHeader* amg;
+    int amg_levels, pad3;
+    void* ph;                    // [n][Q] VT: M^-1 p
+    void* sh;                    // [n][Q] VT: M^-1 s
+    float* vy[kAmgMaxLevels];    // per level [n_l][Q]: pre-smoothed y_l = d_l b_l
+    float* vr[kAmgMaxLevels];    //                     residual r_l
+    float* vb[kAmgMaxLevels];    //                     right-hand side b_l (l >= 1)
+    float* vx[kAmgMaxLevels];    //                     correction x_l (l >= 1)
     double rtol, inner_rtol;
     int maxit, inner_maxit, max_outer, pad2;
 };
@@ -95,7 +106,32 @@ struct Ctl {
     int* stop;
     const int* cancel;
     long long limit;
+    int trace;       // record each step's end time (mvgd_trace_enable)
 };
+
+// ------------------------------------------------------------------------------
+// Step trace: block 0 of the solver stamps the device clock after every grid
+// barrier, with the step it closed, into a static device ring that the host
+// reads with mvgd_trace_read.  Off unless mvgd_trace_enable(1).
+// ------------------------------------------------------------------------------
+constexpr int kTraceMax = 1 << 16;
+static __device__ unsigned long long g_trace[kTraceMax];
+static __device__ unsigned int g_trace_n;
+int g_trace_on = 0;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// step code: Krylov phase ph (0..4), or 0x100 | side << 8 | kind << 4 | level for a V-cycle step
+__device__ __forceinline__ void trace_step(const Ctl& ctl, unsigned code) {
+    if (!ctl.trace || blockIdx.x != 0 || threadIdx.x != 0) return;
+    const unsigned i = g_trace_n;
+    g_trace_n = i + 1;
+    g_trace[i % kTraceMax] = ((unsigned long long)code << 48) | (global_ns() & 0xffffffffffffull);
+}
 
 __device__ __forceinline__ void load_state(RhsState& dst, const RhsState* src) {
     const unsigned long long* s = reinterpret_cast<const unsigned long long*>(src);
@@ -352,10 +388,137 @@ __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, co
 }
 
 // ------------------------------------------------------------------------------
+// Multigrid-preconditioned flow (precond == 2).  Right preconditioning:
+//   p = r + beta (p - omega v);  ph = M^-1 p;  v = A ph;  alpha = rho / (rh, v)
+//   s = r - alpha v;             sh = M^-1 s;  t = A sh;  omega = (t, s) / (t, t)
+//   x += alpha ph + omega sh;    r = s - omega t
+// with M^-1 one V-cycle.  p and s are materialised (the cycle reads them at
+// other rows), with their pre-smoothed FP32 copies y_0 = d_0 p for level 0.
+// ------------------------------------------------------------------------------
+template <bool MIXED, int QT>
+__device__ __forceinline__ void amg_pre_row(const Prob& P, int64_t r, int ph, const RhsState* S,
+                                            const bool (&inner)[QT], const bool (&restart)[QT]) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
+    const int Q = P.Q;
+    const float d0 = P.amg->lv[0].dinv[r];
+    VT* pv = static_cast<VT*>(P.p[0]);
+    const VT* vv = static_cast<const VT*>(P.v[0]);
+    const VT* rv = static_cast<const VT*>(P.r);
+#pragma unroll
+    for (int q = 0; q < QT; q++) {
+        const int64_t e = r * Q + q;
+        if (q >= Q) break;
+        if (ph == P_PRE_A) {
+            if (S[q].pending) {  // the last iteration's step (alpha, omega still hold its values)
+                VT* X = static_cast<VT*>(P.x);
+                X[e] = X[e] + (VT)S[q].alpha * static_cast<const VT*>(P.ph)[e] +
+                       (VT)S[q].omega * static_cast<const VT*>(P.sh)[e];
+            }
+            if (MIXED && restart[q] && S[q].outer > 0 && !S[q].discard)
+                P.u[e] += S[q].scale * (double)static_cast<const VT*>(S[q].fold_best ? P.xb : P.x)[e];
+            if (inner[q]) {
+                const VT nv = rv[e] + (VT)S[q].beta * (pv[e] - (VT)S[q].omega * vv[e]);
+                pv[e] = nv;
+                P.vy[0][e] = d0 * (float)nv;
+            }
+        } else if (inner[q]) {
+            const VT nv = rv[e] - (VT)S[q].alpha * vv[e];
+            static_cast<VT*>(P.s)[e] = nv;
+            P.vy[0][e] = d0 * (float)nv;
+        }
+    }
+}
+
+// A: v = A ph, B: t = A sh, from the staged slice (every lane of the warp calls).
+template <bool MIXED, int QT, typename Landed>
+__device__ __forceinline__ void amg_spmv_row(const Prob& P, int64_t r, bool valid, int ph, const RhsState* S,
+                                             const bool (&on)[QT], F2 (&af)[kChan][QT], double (&ad)[kChan][QT],
+                                             const int* colS,
+                                             const typename std::conditional<MIXED, float, double>::type* valS,
+                                             Landed&& landed) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
+    const int Q = P.Q, k = P.k;
+    const int lane = (int)(r % kSlice);
+    const VT sig = (VT)P.sigma;
+    const VT* src = static_cast<const VT*>(ph == P_A ? P.ph : P.sh);
+    VT si[QT], acc[QT];
+#pragma unroll
+    for (int q = 0; q < QT; q++) {
+        acc[q] = (VT)0;
+        si[q] = (on[q] && valid) ? src[r * Q + q] : (VT)0;
+    }
+    if (!landed() || !valid) return;  // warp-collective
+    const VT w0 = valS[lane];
+#pragma unroll 8
+    for (int sl = 0; sl < k; sl++) {
+        const int64_t j = colS[sl * kSlice + lane];
+        const VT w = valS[(sl + 1) * kSlice + lane];
+#pragma unroll
+        for (int q = 0; q < QT; q++) {
+            if (!on[q]) continue;
+            // FP32: difference form (rows of L sum to zero), as in the plain flow
+            if (MIXED) acc[q] = fmaf(w, src[j * Q + q] - si[q], acc[q]);
+            else acc[q] = fma(w, src[j * Q + q], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QT; q++) {
+        if (!on[q]) continue;
+        const int64_t e = r * Q + q;
+        const VT lx = MIXED ? acc[q] : acc[q] + w0 * si[q];
+        const VT res = sig * si[q] - lx;
+        if (ph == P_A) {
+            static_cast<VT*>(P.v[0])[e] = res;
+            if (MIXED && S[q].best_flag) static_cast<VT*>(P.xb)[e] = static_cast<const VT*>(P.x)[e];
+            const VT rhv = static_cast<const VT*>(P.rh)[e];
+            if (MIXED) f2_add_prod(af[0][q], (float)rhv, (float)res);
+            else ad[0][q] += (double)(rhv * res);
+        } else {
+            static_cast<VT*>(P.t)[e] = res;
+            const VT sv = static_cast<const VT*>(P.s)[e];
+            if (MIXED) {
+                f2_add_prod(af[0][q], (float)res, (float)sv);
+                f2_add_prod(af[1][q], (float)res, (float)res);
+            } else {
+                ad[0][q] += (double)(res * sv);
+                ad[1][q] += (double)(res * res);
+            }
+        }
+    }
+}
+
+// C: r = s - omega t, and (rh, r), (r, r).  The step's x += alpha ph + omega sh
+// waits for the next PRE_A, which applies it only if the residual stayed finite
+// (so a breakdown never reaches x, which is u itself in the FP64 flow).
+template <bool MIXED, int QT>
+__device__ __forceinline__ void amg_c_row(const Prob& P, int64_t r, const RhsState* S, const bool (&inner)[QT],
+                                          F2 (&af)[kChan][QT], double (&ad)[kChan][QT]) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
+    const int Q = P.Q;
+#pragma unroll
+    for (int q = 0; q < QT; q++) {
+        if (!inner[q]) continue;
+        const int64_t e = r * Q + q;
+        const VT om = (VT)S[q].omega;
+        const VT rn = static_cast<const VT*>(P.s)[e] - om * static_cast<const VT*>(P.t)[e];
+        static_cast<VT*>(P.r)[e] = rn;
+        const VT rhv = static_cast<const VT*>(P.rh)[e];
+        if (MIXED) {
+            f2_add_prod(af[0][q], (float)rhv, (float)rn);
+            f2_add_prod(af[1][q], (float)rn, (float)rn);
+        } else {
+            ad[0][q] += (double)(rhv * rn);
+            ad[1][q] += (double)(rn * rn);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------
 // State transitions (run by the block that finishes a request's phase)
 // ------------------------------------------------------------------------------
 template <bool MIXED>
 __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, const Ctl& ctl) {
+    if (ph == P_A) T.pending = 0;  // applied by PRE_A of this iteration
     switch (T.mode) {
         case M_INNER:
             if (ph == P_A) {
@@ -370,6 +533,8 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
                 const double rn = sqrt(b);
                 T.rnorm = rn;
                 const bool finite = isfinite(rn) && isfinite(a);
+                // multigrid flow: x moves by this step only if it stayed finite
+                T.pending = finite ? 1 : 0;
                 // FP32 path: remember the iterate with the smallest residual; an
                 // inner solve that stagnates or starts to diverge ends there and
                 // hands back that best iterate instead of its last one
@@ -463,10 +628,20 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
     }
 }
 
+// Work units of one kind of step: unit c belongs to request chunk_req[c] and
+// is its unit c - chunk_base[request].
+struct ChunkTable {
+    const int* chunk_req;   // [nchunks]
+    const int* chunk_base;  // [count]
+    int nchunks, pad;
+};
+
 struct ReqTable {
-    const Prob* const* prob;  // [count]
-    const int* chunk_req;     // [nchunks]
-    const int* chunk_base;    // [count] first chunk of each request
+    const Prob* const* prob;       // [count]
+    ChunkTable fine;               // kCh-row tiles of level 0 (every Krylov phase; V-cycle level 0)
+    ChunkTable lvl[kAmgMaxLevels]; // [l], 1 <= l < mlev: kCh-row tiles of multigrid level l
+    ChunkTable coarse;             // 8-row groups (a warp each) of every coarsest level
+    int mlev;                      // largest (levels - 1) among the requests
 };
 
 template <typename VT>
@@ -521,8 +696,11 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
     __syncthreads();
 }
 
-template <bool MIXED, int QT>
-__global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2) k_solve(ReqTable tab, int nchunks, Ctl ctl, int iter_budget, int kmax) {
+enum VStep : int { V_DOWN = 0, V_COARSE = 1, V_UP = 2 };
+
+template <bool MIXED, int QT, bool AMG>
+__global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
+    k_solve(ReqTable tab, Ctl ctl, int iter_budget, int kmax) {
     using VT = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char stage_smem[];
     __shared__ RhsState S[QT];
@@ -546,122 +724,224 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2) k_solve(ReqTable ta
     __syncthreads();
     uint32_t parity = 0;   // phase of the warp's mbarrier that the next copy completes
     bool stage_ok = true;  // false once a copy failed to land in time: no more copies are issued
+    auto landed = [&]() {
+        const bool ok = mbar_wait(bar, parity, kStageWaitLimit);
+        parity ^= 1u;
+        stage_ok = __all_sync(0xffffffffu, ok);
+        if (!stage_ok && lane == 0) atomicCAS(ctl.err, 0, (int)MVGD_ETIMEOUT);
+        return stage_ok;
+    };
 
-    for (int it = 0; it < iter_budget; ++it) {
-        // read after the last barrier of the previous iteration: identical in every block
-        const bool pre_a = !MIXED || *(volatile int*)ctl.nrestart > 0;
-        for (int ph = 0; ph < P_COUNT; ++ph) {
-            if (ph == P_PRE_A && !pre_a) continue;
-            if (ph == P_PRE_B && MIXED) continue;
-            const bool reduce = ph == P_A || ph == P_B || ph == P_C;
-            const int slot = red_slot(ph);
-            int cur = -1, tiles = 0, rb = 0;
-            bool inner[QT], restart[QT];
-            bool any_inner = false, any_restart = false, all_done = true;
-            float c1[QT], c2[QT];
-            for (int c = blockIdx.x;; c += gridDim.x) {
-                const int ri = c < nchunks ? tab.chunk_req[c] : -1;
-                if (ri != cur) {
-                    // leaving request `cur`: publish this block's tiles of it
-                    if (cur >= 0 && reduce && tiles > 0)
-                        arrive_and_finalize<MIXED, QT>(*tab.prob[cur], ph, slot, tiles, S, fin, tot, &last, ctl);
-                    if (ri < 0) break;
-                    cur = ri;
-                    tiles = 0;
-                    __syncthreads();
-                    const Prob& P = *tab.prob[ri];
-                    // a K above the one the staging buffers were sized for (a wrong
-                    // req_k) would overrun shared memory: do no work and end the launch
-                    const bool fits = P.k <= kmax;
-                    if (!fits && tid == 0) atomicCAS(ctl.err, 0, (int)MVGD_EINVAL);
-                    if (tid < QT) {
-                        if (tid < P.Q && fits) load_state(S[tid], P.st + tid);
-                        else S[tid].mode = M_DONE;
-                    }
-                    __syncthreads();
-                    any_inner = any_restart = false;
-                    all_done = true;
-#pragma unroll
-                    for (int q = 0; q < QT; q++) {
-                        const int md = S[q].mode;
-                        inner[q] = md == M_INNER;
-                        restart[q] = md == M_RESTART;
-                        any_inner |= inner[q];
-                        any_restart |= restart[q];
-                        all_done &= (md == M_DONE);
-                        c1[q] = (float)(ph == P_A ? S[q].beta : S[q].alpha);
-                        c2[q] = (float)S[q].omega;
-                    }
-                }
-                if (all_done) continue;  // the whole request is finished: no work, no arrival
-                const Prob& P = *tab.prob[ri];
-                const int lc = c - tab.chunk_base[ri];
-                const int64_t r = (int64_t)lc * kCh + tid;
-                const int64_t slice = (int64_t)lc * (kCh / kSlice) + wid;
-                F2 af[kChan][QT];
-                double ad[kChan][QT];
-#pragma unroll
-                for (int ch = 0; ch < kChan; ch++)
-#pragma unroll
-                    for (int q = 0; q < QT; q++) { af[ch][q].hi = 0.0f; af[ch][q].lo = 0.0f; ad[ch][q] = 0.0; }
-                // warp-uniform: lane 0 stages the whole slice and every lane waits for it
-                const bool staged = (ph == P_A || ph == P_B) && any_inner && slice * kSlice < P.n && stage_ok;
-                if (staged) {
-                    stage_slice<VT>(P, slice, colS, valS, bar, pol);
-                    spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, c1, c2, af, ad, colS, valS, [&]() {
-                        const bool ok = mbar_wait(bar, parity, kStageWaitLimit);
-                        parity ^= 1u;
-                        stage_ok = __all_sync(0xffffffffu, ok);
-                        if (!stage_ok && lane == 0) atomicCAS(ctl.err, 0, (int)MVGD_ETIMEOUT);
-                        return stage_ok;
-                    });
-                }
-                if (r < P.n) {
-                    // a restart computes its residual in A and resets the Krylov vectors in C,
-                    // so that its first inner step starts at the next iteration's A
-                    if (ph == P_A || ph == P_B) {
-                        if (any_restart && ph == P_A) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
-                    } else if (ph == P_C) {
-                        if (any_inner) {
-                            if (MIXED) elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
-                            else c_row_f64<QT>(P, r, S, inner, ad);
-                        }
-                        if (any_restart) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
-                    } else {
-                        elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
-                    }
-                }
-                if (!reduce) continue;
-                // tile partials in a fixed order: FP32 partials within the warp in FP32,
-                // then the 8 warps in order; `red` alternates so one barrier per tile suffices
-#pragma unroll
-                for (int ch = 0; ch < kChan; ch++)
-#pragma unroll
-                    for (int q = 0; q < QT; q++) {
-                        double v = f2_to_double(warp_sum_f2(af[ch][q]));
-                        if (any_restart || !MIXED) v += warp_sum(ad[ch][q]);
-                        if (lane == 0) red[rb][wid][ch * QT + q] = v;
-                    }
-                __syncthreads();
-                if (tid < kChan * QT) {
-                    double v = 0.0;
-                    for (int w = 0; w < kThreads / 32; w++) v += red[rb][w][tid];
-                    const int ch = tid / QT, q = tid % QT;
-                    if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + lc) * P.Q + q] = v;
-                }
-                rb ^= 1;
-                tiles++;
-            }
-            // the stop word is written only before the last barrier of an iteration and
-            // read only after it, so every block takes the same exit decision
-            if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
-                *ctl.stop = 1;
-            if (!grid_sync(ctl.bar, ctl.err, ctl.limit)) {
-                it = iter_budget;  // error exit, after the drain below
-                break;
+    bool inner[QT], restart[QT];
+    bool any_inner = false, any_restart = false, all_done = true;
+    float c1[QT], c2[QT];
+    // Loads request ri's per-RHS state into S (block-wide) and its masks.
+    auto enter = [&](int ri, int ph) {
+        __syncthreads();
+        const Prob& P = *tab.prob[ri];
+        // a K above the one the staging buffers were sized for (a wrong K in the
+        // request list) would overrun shared memory, and a hierarchy of another
+        // operator would be read out of bounds: do no work and end the launch
+        bool fits = P.k <= kmax && ((P.amg != nullptr) == AMG);
+        if (AMG && fits) fits = P.amg->n == P.n && P.amg->k == P.k;
+        if (!fits && tid == 0) atomicCAS(ctl.err, 0, (int)MVGD_EINVAL);
+        if (tid < QT) {
+            if (tid < P.Q && fits) {
+                load_state(S[tid], P.st + tid);
+            } else {  // a slot past the request's RHS count: no work of any kind
+                S[tid].mode = M_DONE;
+                S[tid].pending = 0;
             }
         }
-        if (it < iter_budget && (*(volatile int*)ctl.active == 0 || *(volatile int*)ctl.stop != 0)) break;
+        __syncthreads();
+        any_inner = any_restart = false;
+        all_done = true;
+#pragma unroll
+        for (int q = 0; q < QT; q++) {
+            const int md = S[q].mode;
+            inner[q] = md == M_INNER;
+            restart[q] = md == M_RESTART;
+            any_inner |= inner[q];
+            any_restart |= restart[q];
+            all_done &= (md == M_DONE);
+            c1[q] = (float)(ph == P_A ? S[q].beta : S[q].alpha);
+            c2[q] = (float)S[q].omega;
+        }
+    };
+
+    // One Krylov phase over every request's level-0 tiles, then the grid barrier.
+    auto fine_phase = [&](int ph) -> bool {
+        const bool reduce = ph == P_A || ph == P_B || ph == P_C;
+        const int slot = red_slot(ph);
+        int cur = -1, tiles = 0, rb = 0;
+        for (int c = blockIdx.x;; c += gridDim.x) {
+            const int ri = c < tab.fine.nchunks ? tab.fine.chunk_req[c] : -1;
+            if (ri != cur) {
+                // leaving request `cur`: publish this block's tiles of it
+                if (cur >= 0 && reduce && tiles > 0)
+                    arrive_and_finalize<MIXED, QT>(*tab.prob[cur], ph, slot, tiles, S, fin, tot, &last, ctl);
+                if (ri < 0) break;
+                cur = ri;
+                tiles = 0;
+                enter(ri, ph);
+            }
+            if (all_done) continue;  // the whole request is finished: no work, no arrival
+            const Prob& P = *tab.prob[ri];
+            const int lc = c - tab.fine.chunk_base[ri];
+            const int64_t r = (int64_t)lc * kCh + tid;
+            const int64_t slice = (int64_t)lc * (kCh / kSlice) + wid;
+            F2 af[kChan][QT];
+            double ad[kChan][QT];
+#pragma unroll
+            for (int ch = 0; ch < kChan; ch++)
+#pragma unroll
+                for (int q = 0; q < QT; q++) { af[ch][q].hi = 0.0f; af[ch][q].lo = 0.0f; ad[ch][q] = 0.0; }
+            // warp-uniform: lane 0 stages the whole slice and every lane waits for it
+            const bool staged = (ph == P_A || ph == P_B) && any_inner && slice * kSlice < P.n && stage_ok;
+            if (staged) {
+                stage_slice<VT>(P, slice, colS, valS, bar, pol);
+                if (AMG) amg_spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, af, ad, colS, valS, landed);
+                else spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, c1, c2, af, ad, colS, valS, landed);
+            }
+            if (r < P.n) {
+                // a restart computes its residual in A and resets the Krylov vectors in C,
+                // so that its first inner step starts at the next iteration's A
+                if (ph == P_A || ph == P_B) {
+                    if (any_restart && ph == P_A) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
+                } else if (ph == P_C) {
+                    if (any_inner) {
+                        if (AMG) amg_c_row<MIXED, QT>(P, r, S, inner, af, ad);
+                        else if (MIXED) elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
+                        else c_row_f64<QT>(P, r, S, inner, ad);
+                    }
+                    if (any_restart) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
+                } else {
+                    if (AMG) amg_pre_row<MIXED, QT>(P, r, ph, S, inner, restart);
+                    else elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
+                }
+            }
+            if (!reduce) continue;
+            // tile partials in a fixed order: FP32 partials within the warp in FP32,
+            // then the 8 warps in order; `red` alternates so one barrier per tile suffices
+#pragma unroll
+            for (int ch = 0; ch < kChan; ch++)
+#pragma unroll
+                for (int q = 0; q < QT; q++) {
+                    double v = f2_to_double(warp_sum_f2(af[ch][q]));
+                    if (any_restart || !MIXED) v += warp_sum(ad[ch][q]);
+                    if (lane == 0) red[rb][wid][ch * QT + q] = v;
+                }
+            __syncthreads();
+            if (tid < kChan * QT) {
+                double v = 0.0;
+                for (int w = 0; w < kThreads / 32; w++) v += red[rb][w][tid];
+                const int ch = tid / QT, q = tid % QT;
+                if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + lc) * P.Q + q] = v;
+            }
+            rb ^= 1;
+            tiles++;
+        }
+        // the stop word is written only before the last barrier of an iteration and
+        // read only after it, so every block takes the same exit decision
+        if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
+            *ctl.stop = 1;
+        const bool ok = grid_sync(ctl.bar, ctl.err, ctl.limit);
+        trace_step(ctl, (unsigned)ph);
+        return ok;
+    };
+
+    // One step of the V-cycle applied to p (side 0) or s (side 1) of every
+    // INNER right-hand side, then the grid barrier.
+    auto vstep = [&](int kind, int l, int side) -> bool {
+        const ChunkTable& T = kind == V_COARSE ? tab.coarse : (l == 0 ? tab.fine : tab.lvl[l]);
+        int cur = -1;
+        for (int c = blockIdx.x; c < T.nchunks; c += gridDim.x) {
+            const int ri = T.chunk_req[c];
+            if (ri != cur) {
+                cur = ri;
+                enter(ri, P_PRE_A);
+            }
+            const Prob& P = *tab.prob[ri];
+            const int m = P.amg_levels - 1;  // the request's coarsest level
+            if (!any_inner || (kind != V_COARSE && l >= m)) continue;
+            const AmgHeader& H = *P.amg;
+            const int Q = P.Q;
+            const int lc = c - T.chunk_base[ri];
+            const VT* B0 = static_cast<const VT*>(side == 0 ? P.p[0] : P.s);
+            VT* X0 = static_cast<VT*>(side == 0 ? P.ph : P.sh);
+            if (kind == V_COARSE) {
+                const int64_t rho = (int64_t)lc * (kThreads / kWarp) + wid;  // a warp per row
+                if (rho >= H.nc) continue;
+#pragma unroll
+                for (int q = 0; q < QT; q++) {
+                    if (!inner[q]) continue;
+                    float x;
+                    if (m == 0) x = coarse_row(H, rho, [&](int64_t cc) { return (float)B0[cc * Q + q]; });
+                    else x = coarse_row(H, rho, [&](int64_t cc) { return P.vb[m][cc * Q + q]; });
+                    if (lane == 0) {
+                        if (m == 0) X0[rho * Q + q] = (VT)x;
+                        else P.vx[m][rho * Q + q] = x;
+                    }
+                }
+                continue;
+            }
+            const int64_t nl = H.lv[l].n;
+            const int64_t r = (int64_t)lc * kCh + tid;
+            if (r - lane >= nl) continue;  // whole warps past the level's end
+            const bool valid = r < nl;
+            if (kind == V_DOWN) {
+                float* Yn = (l + 1 < m) ? P.vy[l + 1] : nullptr;
+#pragma unroll
+                for (int q = 0; q < QT; q++) {
+                    if (!inner[q]) continue;
+                    const float* Y = P.vy[l];
+                    const float bi = valid ? (l == 0 ? (float)B0[r * Q + q] : P.vb[l][r * Q + q]) : 0.0f;
+                    const float yi = valid ? Y[r * Q + q] : 0.0f;
+                    vdown_row(H, l, r, valid, Q, q, bi, yi, [&](int64_t j) { return Y[j * Q + q]; }, P.vr[l],
+                              P.vb[l + 1], Yn);
+                }
+            } else if (valid) {
+                const float* Xc = P.vx[l + 1];
+#pragma unroll
+                for (int q = 0; q < QT; q++) {
+                    if (!inner[q]) continue;
+                    const int64_t e = r * Q + q;
+                    const float x = vup_row(H, l, r, Q, q, P.vy[l][e], P.vr[l][e],
+                                            [&](int64_t J) { return Xc[J * Q + q]; });
+                    if (l == 0) X0[e] = (VT)x;
+                    else P.vx[l][e] = x;
+                }
+            }
+        }
+        const bool ok = grid_sync(ctl.bar, ctl.err, ctl.limit);
+        trace_step(ctl, 0x100u | ((unsigned)side << 8) | ((unsigned)kind << 4) | (unsigned)l);
+        return ok;
+    };
+    auto vcycle = [&](int side) -> bool {
+        for (int l = 0; l < tab.mlev; l++)
+            if (!vstep(V_DOWN, l, side)) return false;
+        if (!vstep(V_COARSE, 0, side)) return false;
+        for (int l = tab.mlev - 1; l >= 0; l--)
+            if (!vstep(V_UP, l, side)) return false;
+        return true;
+    };
+
+    for (int it = 0; it < iter_budget; ++it) {
+        bool ok = true;
+        if (AMG) {
+            ok = fine_phase(P_PRE_A) && vcycle(0) && fine_phase(P_A) && fine_phase(P_PRE_B) && vcycle(1) &&
+                 fine_phase(P_B) && fine_phase(P_C);
+        } else {
+            // read after the last barrier of the previous iteration: identical in every block
+            const bool pre_a = !MIXED || *(volatile int*)ctl.nrestart > 0;
+            for (int ph = 0; ph < P_COUNT && ok; ++ph) {
+                if (ph == P_PRE_A && !pre_a) continue;
+                if (ph == P_PRE_B && MIXED) continue;
+                ok = fine_phase(ph);
+            }
+        }
+        if (!ok) break;  // error exit, after the drain below
+        if (*(volatile int*)ctl.active == 0 || *(volatile int*)ctl.stop != 0) break;
     }
     // a copy that missed its wait may still be landing: give it one more bounded
     // wait before the block's shared memory is released
@@ -681,12 +961,18 @@ struct ReqLayout {
     double* us;
     double* r64;
     void* invd;
-    void* vec[10];  // x r rh p0 p1 v0 v1 s t x_best
+    void* vec[12];  // x r rh p0 p1 v0 v1 s t x_best ph sh
+    int nlev;       // multigrid levels (precond == 2), else 0
+    float* vy[kAmgMaxLevels];
+    float* vr[kAmgMaxLevels];
+    float* vb[kAmgMaxLevels];
+    float* vx[kAmgMaxLevels];
     size_t bytes;
 };
 
-ReqLayout req_layout(void* ws, int64_t n, int Q, int prec) {
+ReqLayout req_layout(void* ws, int64_t n, int Q, int prec, int precond) {
     ReqLayout L;
+    memset(&L, 0, sizeof(L));
     Carver cv(ws);
     const int64_t nchunk = (n + kCh - 1) / kCh;
     const size_t vt = prec == MVGD_FP64 ? sizeof(double) : sizeof(float);
@@ -699,28 +985,52 @@ ReqLayout req_layout(void* ws, int64_t n, int Q, int prec) {
     L.us = cv.take<double>(n * Q);
     L.r64 = cv.take<double>(n * Q);
     L.invd = cv.take<char>(vt * n);
-    for (int v = 0; v < 10; v++) L.vec[v] = cv.take<char>(vt * n * Q);
+    const int nvec = precond == 2 ? 12 : 10;
+    for (int v = 0; v < nvec; v++) L.vec[v] = cv.take<char>(vt * n * Q);
+    if (precond == 2) {
+        int64_t sizes[kAmgMaxLevels];
+        L.nlev = amg_levels(n, sizes);
+        for (int l = 0; l < L.nlev; l++) {
+            const int64_t m = n_padded(sizes[l]) * Q;
+            L.vy[l] = cv.take<float>(m);
+            L.vr[l] = cv.take<float>(m);
+            if (l > 0) {
+                L.vb[l] = cv.take<float>(m);
+                L.vx[l] = cv.take<float>(m);
+            }
+        }
+    }
     L.bytes = cv.used;
     return L;
 }
 
+// Chunk tables of one launch: level 0 (Krylov phases), levels 1 .. kAmgMaxLevels-1
+// and the coarsest solves; each with its per-request first-unit array.
 struct CtlLayout {
     unsigned* bar;
     int* words;     // err, active, nrestart, stop
     const Prob** prob;
-    int* chunk_req;
-    int* chunk_base;
+    int* chunk_req[kAmgMaxLevels + 1];   // [0] fine, [l] level l, [kAmgMaxLevels] coarsest
+    int* chunk_base[kAmgMaxLevels + 1];
     size_t bytes;
 };
 
+constexpr int kCoarseUnits = (kAmgCoarsest + kThreads / kWarp - 1) / (kThreads / kWarp);
+
 CtlLayout ctl_layout(void* ws, int max_req, int64_t max_chunks) {
     CtlLayout C;
+    memset(&C, 0, sizeof(C));
     Carver cv(ws);
     C.bar = cv.take<unsigned>(2);
     C.words = cv.take<int>(4);
     C.prob = cv.take<const Prob*>(max_req);
-    C.chunk_req = cv.take<int>(max_chunks);
-    C.chunk_base = cv.take<int>(max_req);
+    for (int t = 0; t <= kAmgMaxLevels; t++) {
+        // level l >= 1 has at most max_chunks / 8^l + max_req tiles; the bound below is looser
+        const int64_t units = t == kAmgMaxLevels ? (int64_t)max_req * kCoarseUnits
+                                                  : (t == 0 ? max_chunks : max_chunks / kAmgAgg + max_req);
+        C.chunk_req[t] = cv.take<int>(units);
+        C.chunk_base[t] = cv.take<int>(max_req);
+    }
     C.bytes = cv.used;
     return C;
 }
@@ -744,7 +1054,7 @@ __global__ void k_request_init(Prob P, Prob* dst, int64_t n) {
         T.status = MVGD_OK;
         T.discard = 0;
         T.stall = 0;
-        T.best_flag = T.fold_best = T.since_best = T.pad1 = 0;
+        T.best_flag = T.fold_best = T.since_best = T.pending = 0;
         P.st[threadIdx.x] = T;
     }
     if (blockIdx.x == 0 && threadIdx.x < kRedSlots) P.arrive[threadIdx.x] = 0;
@@ -828,7 +1138,7 @@ __global__ void k_build_table(TableArgs A, int base, const Prob** prob, int* chu
     }
     __syncthreads();
     for (int i = threadIdx.x; i < A.count; i += blockDim.x) {
-        prob[base + i] = A.prob[i];
+        if (prob) prob[base + i] = A.prob[i];
         chunk_base[base + i] = start[i];
     }
     for (int i = 0; i < A.count; i++)
@@ -883,10 +1193,10 @@ __global__ void k_poll(TableArgs A, int32_t* done) {
     }
 }
 
-template <bool MIXED, int QT>
-mvgd_status launch_solve(ReqTable tab, int nchunks, Ctl ctl, int budget, int kmax, cudaStream_t s) {
+template <bool MIXED, int QT, bool AMG>
+mvgd_status launch_solve(const ReqTable& tab, Ctl ctl, int budget, int kmax, cudaStream_t s) {
     using VT = typename std::conditional<MIXED, float, double>::type;
-    auto fn = k_solve<MIXED, QT>;
+    auto fn = k_solve<MIXED, QT, AMG>;
     const size_t smem = stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp);
     int dev = 0, sms = 0, per_sm = 0;
     MVGD_CUDA_TRY(cudaGetDevice(&dev));
@@ -895,18 +1205,19 @@ mvgd_status launch_solve(ReqTable tab, int nchunks, Ctl ctl, int budget, int kma
     MVGD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
     if (per_sm < 1) return MVGD_ECUDA;
     int grid = sms * per_sm;
-    if (grid > nchunks) grid = nchunks;
-    void* args[] = {(void*)&tab, (void*)&nchunks, (void*)&ctl, (void*)&budget, (void*)&kmax};
+    if (grid > tab.fine.nchunks) grid = tab.fine.nchunks;
+    ReqTable t = tab;
+    void* args[] = {(void*)&t, (void*)&ctl, (void*)&budget, (void*)&kmax};
     MVGD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, smem, s));
     return MVGD_OK;
 }
 
-template <bool MIXED>
-mvgd_status dispatch_q(int Q, ReqTable tab, int nchunks, Ctl ctl, int budget, int kmax, cudaStream_t s) {
-    if (Q <= 1) return launch_solve<MIXED, 1>(tab, nchunks, ctl, budget, kmax, s);
-    if (Q <= 2) return launch_solve<MIXED, 2>(tab, nchunks, ctl, budget, kmax, s);
-    if (Q <= 4) return launch_solve<MIXED, 4>(tab, nchunks, ctl, budget, kmax, s);
-    return launch_solve<MIXED, 8>(tab, nchunks, ctl, budget, kmax, s);
+template <bool MIXED, bool AMG>
+mvgd_status dispatch_q(int Q, const ReqTable& tab, Ctl ctl, int budget, int kmax, cudaStream_t s) {
+    if (Q <= 1) return launch_solve<MIXED, 1, AMG>(tab, ctl, budget, kmax, s);
+    if (Q <= 2) return launch_solve<MIXED, 2, AMG>(tab, ctl, budget, kmax, s);
+    if (Q <= 4) return launch_solve<MIXED, 4, AMG>(tab, ctl, budget, kmax, s);
+    return launch_solve<MIXED, 8, AMG>(tab, ctl, budget, kmax, s);
 }
 
 int gather_blocks(int64_t elems) {
@@ -924,10 +1235,11 @@ using namespace mvgd;
 // ---------------------------------------------------------------------------------
 // Requests
 // ---------------------------------------------------------------------------------
-MVGD_API size_t mvgd_request_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec) {
+MVGD_API size_t mvgd_request_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec, int32_t precond) {
     (void)k;
-    if (n <= 0 || nrhs < 1 || nrhs > 8) return 0;
-    return req_layout(nullptr, n, nrhs, prec).bytes;
+    if (n <= 0 || nrhs < 1 || nrhs > 8 || precond < 0 || precond > 2) return 0;
+    if (precond == 2 && amg_levels(n, nullptr) == 0) return 0;
+    return req_layout(nullptr, n, nrhs, prec, precond).bytes;
 }
 
 MVGD_API mvgd_status mvgd_request_init(void* req_ws, size_t req_bytes, const mvgd_ell* L, int32_t nrhs, double sigma,
@@ -941,10 +1253,12 @@ MVGD_API mvgd_status mvgd_request_init(void* req_ws, size_t req_bytes, const mvg
         !aligned(L->val_lo) || !aligned(L->order))
         return MVGD_EINVAL;
     if (!(opts->rtol > 0) || opts->maxit < 1 || !(sigma == sigma)) return MVGD_EINVAL;
+    if (opts->precond < 0 || opts->precond > 2) return MVGD_EINVAL;
+    if (opts->precond == 2 && (!opts->amg || !aligned(opts->amg))) return MVGD_EINVAL;
     const bool mixed = L->prec == MVGD_FP32_REFINE;
     if (mixed && (opts->inner_maxit < 1 || !(opts->inner_rtol > 0) || opts->max_outer < 1)) return MVGD_EINVAL;
     const int64_t n = L->n;
-    ReqLayout W = req_layout(req_ws, n, nrhs, L->prec);
+    ReqLayout W = req_layout(req_ws, n, nrhs, L->prec, opts->precond);
     if (req_bytes < W.bytes) return MVGD_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     const int gb = gather_blocks(n * nrhs);
@@ -986,6 +1300,17 @@ MVGD_API mvgd_status mvgd_request_init(void* req_ws, size_t req_bytes, const mvg
     P.inner_maxit = mixed ? opts->inner_maxit : opts->maxit;
     P.max_outer = mixed ? opts->max_outer : 1000;
     P.pad2 = 0;
+    P.amg = opts->precond == 2 ? static_cast<const AmgHeader*>(opts->amg) : nullptr;
+    P.amg_levels = W.nlev;
+    P.pad3 = 0;
+    P.ph = W.vec[10];
+    P.sh = W.vec[11];
+    for (int l = 0; l < kAmgMaxLevels; l++) {
+        P.vy[l] = W.vy[l];
+        P.vr[l] = W.vr[l];
+        P.vb[l] = W.vb[l];
+        P.vx[l] = W.vx[l];
+    }
     k_request_init<<<1, 32, 0, s>>>(P, W.prob, n);
     if (P.precond) k_prep_scaling<<<gather_blocks(n), 256, 0, s>>>(P);
     return launch_status();
@@ -996,38 +1321,64 @@ MVGD_API size_t mvgd_iterate_workspace_bytes(int32_t max_requests, int64_t max_t
     return ctl_layout(nullptr, max_requests, max_chunks_for(max_requests, max_total_rows)).bytes;
 }
 
-MVGD_API mvgd_status mvgd_iterate(void* const* reqs, const int64_t* req_rows, const int32_t* req_nrhs,
-                                  const int32_t* req_k, int32_t count, int32_t prec, int32_t max_iterations,
-                                  const int32_t* cancel, void* ctl_ws, size_t ctl_bytes, mvgd_stream_t stream) {
-    if (!reqs || !req_rows || !req_nrhs || !req_k || count < 1 || count > kMaxReq || max_iterations < 0 || !ctl_ws)
-        return MVGD_EINVAL;
+MVGD_API mvgd_status mvgd_iterate(const mvgd_request* reqs, int32_t count, int32_t prec, int32_t precond,
+                                  int32_t max_iterations, const int32_t* cancel, void* ctl_ws, size_t ctl_bytes,
+                                  mvgd_stream_t stream) {
+    if (!reqs || count < 1 || count > kMaxReq || max_iterations < 0 || !ctl_ws) return MVGD_EINVAL;
     if (prec != MVGD_FP64 && prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    if (precond < 0 || precond > 2) return MVGD_EINVAL;
+    const bool amg = precond == 2;
     int64_t total_rows = 0;
-    int maxQ = 1, kmax = kMinK;
+    int maxQ = 1, kmax = kMinK, mlev = 0;
     for (int i = 0; i < count; i++) {
-        if (!reqs[i] || !aligned(reqs[i]) || req_rows[i] < 1 || req_rows[i] >= (1ll << 31) || req_nrhs[i] < 1 ||
-            req_nrhs[i] > 8 || req_k[i] < kMinK || req_k[i] > kMaxK)
+        const mvgd_request& R = reqs[i];
+        if (!R.workspace || !aligned(R.workspace) || R.n < 2 || R.n >= (1ll << 31) || R.nrhs < 1 || R.nrhs > 8 ||
+            R.k < kMinK || R.k > kMaxK)
             return MVGD_EINVAL;
-        total_rows += req_rows[i];
-        if (req_nrhs[i] > maxQ) maxQ = req_nrhs[i];
-        if (req_k[i] > kmax) kmax = req_k[i];
+        total_rows += R.n;
+        if (R.nrhs > maxQ) maxQ = R.nrhs;
+        if (R.k > kmax) kmax = R.k;
+        if (amg) {
+            const int nl = amg_levels(R.n, nullptr);
+            if (nl == 0) return MVGD_EINVAL;
+            if (nl - 1 > mlev) mlev = nl - 1;
+        }
     }
     if (!aligned(ctl_ws) || !aligned(cancel)) return MVGD_EINVAL;
     if (ctl_bytes < mvgd_iterate_workspace_bytes(count, total_rows)) return MVGD_EWORKSPACE;
     if (max_iterations == 0) return MVGD_OK;
     cudaStream_t s = (cudaStream_t)stream;
     CtlLayout C = ctl_layout(ctl_ws, count, max_chunks_for(count, total_rows));
-    int nchunks = 0;
-    for (int g = 0; g < count; g += kTableMax) {
-        TableArgs A;
-        A.count = count - g < kTableMax ? count - g : kTableMax;
-        A.first_chunk = nchunks;
-        for (int i = 0; i < A.count; i++) {
-            A.prob[i] = reinterpret_cast<const Prob*>(reqs[g + i]);  // the Prob record opens every request workspace
-            A.nchunk[i] = (int)((req_rows[g + i] + kCh - 1) / kCh);
-            nchunks += A.nchunk[i];
+    ReqTable tab;
+    memset(&tab, 0, sizeof(tab));
+    tab.prob = C.prob;
+    tab.mlev = mlev;
+    // table t: 0 = level-0 tiles, 1 .. mlev-1 = level-t tiles, kAmgMaxLevels = coarsest rows by 8
+    for (int t = 0; t <= kAmgMaxLevels; t++) {
+        const bool coarse = t == kAmgMaxLevels;
+        if (t > 0 && (!amg || (!coarse && t >= mlev))) continue;
+        int units = 0;
+        for (int g = 0; g < count; g += kTableMax) {
+            TableArgs A;
+            A.count = count - g < kTableMax ? count - g : kTableMax;
+            A.first_chunk = units;
+            for (int i = 0; i < A.count; i++) {
+                const mvgd_request& R = reqs[g + i];
+                A.prob[i] = reinterpret_cast<const Prob*>(R.workspace);  // the Prob record opens every workspace
+                int64_t sizes[kAmgMaxLevels];
+                const int nl = amg ? amg_levels(R.n, sizes) : 1;
+                if (t == 0) A.nchunk[i] = (int)((R.n + kCh - 1) / kCh);
+                else if (coarse) A.nchunk[i] = (int)((sizes[nl - 1] + kThreads / kWarp - 1) / (kThreads / kWarp));
+                else A.nchunk[i] = t < nl - 1 ? (int)((sizes[t] + kCh - 1) / kCh) : 0;
+                units += A.nchunk[i];
+            }
+            k_build_table<<<1, 256, 0, s>>>(A, g, t == 0 ? C.prob : nullptr, C.chunk_req[t], C.chunk_base[t], C.bar,
+                                            C.words, t == 0 && g == 0);
         }
-        k_build_table<<<1, 256, 0, s>>>(A, g, C.prob, C.chunk_req, C.chunk_base, C.bar, C.words, g == 0);
+        ChunkTable& T = coarse ? tab.coarse : (t == 0 ? tab.fine : tab.lvl[t]);
+        T.chunk_req = C.chunk_req[t];
+        T.chunk_base = C.chunk_base[t];
+        T.nchunks = units;
     }
     k_count_active<<<1, 256, 0, s>>>(C.prob, count, C.words);
     Ctl ctl;
@@ -1039,12 +1390,14 @@ MVGD_API mvgd_status mvgd_iterate(void* const* reqs, const int64_t* req_rows, co
     ctl.stop = C.words + 3;
     ctl.cancel = cancel;
     ctl.limit = 20000000ll;  // polls of >= 32 ns each: seconds, never reached by co-resident blocks
-    ReqTable tab;
-    tab.prob = C.prob;
-    tab.chunk_req = C.chunk_req;
-    tab.chunk_base = C.chunk_base;
-    mvgd_status st = prec == MVGD_FP32_REFINE ? dispatch_q<true>(maxQ, tab, nchunks, ctl, max_iterations, kmax, s)
-                                              : dispatch_q<false>(maxQ, tab, nchunks, ctl, max_iterations, kmax, s);
+    ctl.trace = g_trace_on;
+    mvgd_status st;
+    if (prec == MVGD_FP32_REFINE)
+        st = amg ? dispatch_q<true, true>(maxQ, tab, ctl, max_iterations, kmax, s)
+                 : dispatch_q<true, false>(maxQ, tab, ctl, max_iterations, kmax, s);
+    else
+        st = amg ? dispatch_q<false, true>(maxQ, tab, ctl, max_iterations, kmax, s)
+                 : dispatch_q<false, false>(maxQ, tab, ctl, max_iterations, kmax, s);
     if (st != MVGD_OK) return st;
     k_mark_exit<<<1, 256, 0, s>>>(C.prob, count, C.words);
     return launch_status();
@@ -1081,10 +1434,16 @@ MVGD_API mvgd_status mvgd_request_finish(void* req_ws, int64_t n, int32_t nrhs, 
 // ---------------------------------------------------------------------------------
 // One system: init + iterate to the end + finish
 // ---------------------------------------------------------------------------------
-MVGD_API size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec) {
+MVGD_API size_t mvgd_solve_workspace_bytes(int64_t n, int32_t k, int32_t nrhs, int32_t prec, int32_t precond) {
     if (n <= 0 || nrhs < 1 || nrhs > 8) return 0;
-    return mvgd_request_workspace_bytes(n, k, nrhs, prec) + mvgd_iterate_workspace_bytes(1, n) +
-           align_up(sizeof(mvgd_solve_info) * 8);
+    const size_t req = mvgd_request_workspace_bytes(n, k, nrhs, prec, precond);
+    if (req == 0) return 0;
+    size_t amg = 0;
+    if (precond == 2) {
+        amg = mvgd_amg_workspace_bytes(n, k);
+        if (amg == 0) return 0;
+    }
+    return req + mvgd_iterate_workspace_bytes(1, n) + align_up(sizeof(mvgd_solve_info) * 8) + align_up(amg);
 }
 
 MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, const double* f, double* u,
@@ -1097,28 +1456,42 @@ MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, c
     if (L->prec == MVGD_FP32_REFINE &&
         (!L->val_lo || opts->inner_maxit < 1 || !(opts->inner_rtol > 0) || opts->max_outer < 1))
         return MVGD_EINVAL;
-    const size_t need = mvgd_solve_workspace_bytes(L->n, L->k, nrhs, L->prec);
+    if (opts->precond < 0 || opts->precond > 2 || (opts->amg && !aligned(opts->amg))) return MVGD_EINVAL;
+    size_t need = mvgd_solve_workspace_bytes(L->n, L->k, nrhs, L->prec, opts->precond);
+    if (need == 0) return MVGD_EINVAL;
+    if (opts->precond == 2 && opts->amg) need -= align_up(mvgd_amg_workspace_bytes(L->n, L->k));  // not built here
     if (!aligned(ws) || !aligned(u) || !aligned(f)) return MVGD_EINVAL;
     if (ws_bytes < need) return MVGD_EWORKSPACE;
     cudaPointerAttributes pa;
     MVGD_CUDA_TRY(cudaPointerGetAttributes(&pa, info));
     const bool host_info = pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged;
     char* base = static_cast<char*>(ws);
-    const size_t req_bytes = mvgd_request_workspace_bytes(L->n, L->k, nrhs, L->prec);
+    const size_t req_bytes = mvgd_request_workspace_bytes(L->n, L->k, nrhs, L->prec, opts->precond);
     const size_t ctl_bytes = mvgd_iterate_workspace_bytes(1, L->n);
     void* req = base;
     void* ctl = base + req_bytes;
     mvgd_solve_info* staged = reinterpret_cast<mvgd_solve_info*>(base + req_bytes + ctl_bytes);
-    mvgd_status st = mvgd_request_init(req, req_bytes, L, nrhs, sigma, f, u, opts, stream);
+    mvgd_solve_opts o = *opts;
+    mvgd_status st;
+    if (o.precond == 2 && !o.amg) {
+        // no hierarchy given: build one after the info staging area
+        void* amg = base + req_bytes + ctl_bytes + align_up(sizeof(mvgd_solve_info) * 8);
+        st = mvgd_amg_setup(L, sigma, amg, mvgd_amg_workspace_bytes(L->n, L->k), stream);
+        if (st != MVGD_OK) return st;
+        o.amg = amg;
+    }
+    st = mvgd_request_init(req, req_bytes, L, nrhs, sigma, f, u, &o, stream);
     if (st != MVGD_OK) return st;
     // every inner iteration and every restart is one pass of the phases
     const bool mixed = L->prec == MVGD_FP32_REFINE;
     long long budget = (long long)opts->maxit + 2ll * ((mixed ? opts->max_outer : 1000) + 2) + 4;
     if (budget > (1ll << 30)) budget = 1ll << 30;
-    int64_t rows = L->n;
-    int32_t q = nrhs;
-    void* reqs[1] = {req};
-    st = mvgd_iterate(reqs, &rows, &q, &L->k, 1, L->prec, (int32_t)budget, cancel, ctl, ctl_bytes, stream);
+    mvgd_request one;
+    one.workspace = req;
+    one.n = L->n;
+    one.nrhs = nrhs;
+    one.k = L->k;
+    st = mvgd_iterate(&one, 1, L->prec, o.precond, (int32_t)budget, cancel, ctl, ctl_bytes, stream);
     if (st != MVGD_OK) return st;
     st = mvgd_request_finish(req, L->n, nrhs, u, host_info ? staged : info, stream);
     if (st != MVGD_OK) return st;
@@ -1130,4 +1503,26 @@ MVGD_API mvgd_status mvgd_solve(const mvgd_ell* L, int32_t nrhs, double sigma, c
     for (int i = 0; i < nrhs; i++)
         if (info[i].status != MVGD_OK && worst == MVGD_OK) worst = info[i].status;
     return (mvgd_status)worst;
+}
+
+// ---------------------------------------------------------------------------------
+// Step trace
+// ---------------------------------------------------------------------------------
+MVGD_API mvgd_status mvgd_trace_enable(int32_t on) {
+    g_trace_on = on ? 1 : 0;
+    if (on) {
+        const unsigned zero = 0;
+        MVGD_CUDA_TRY(cudaMemcpyToSymbol(g_trace_n, &zero, sizeof(zero)));
+    }
+    return MVGD_OK;
+}
+
+MVGD_API int32_t mvgd_trace_read(uint64_t* out, int32_t max) {
+    if (!out || max < 1) return -1;
+    unsigned n = 0;
+    if (cudaMemcpyFromSymbol(&n, g_trace_n, sizeof(n)) != cudaSuccess) return -1;
+    const int32_t count = (int32_t)(n < (unsigned)kTraceMax ? n : (unsigned)kTraceMax);
+    const int32_t take = count < max ? count : max;
+    if (take > 0 && cudaMemcpyFromSymbol(out, g_trace, sizeof(uint64_t) * take) != cudaSuccess) return -1;
+    return take;
 }

@@ -1,0 +1,96 @@
+// Row steps of one V(1,1)-cycle of the aggregation multigrid hierarchy (FP32),
+// shared by the standalone application (amg.cu) and the persistent solver
+// (solve.cu).  One lane per row; a warp holds 32 consecutive rows of a level,
+// so the 8 rows of an aggregate sit in 8 consecutive lanes and restriction is
+// a shuffle sum inside each group of 8.  Vectors are [rows][Q] FP32,
+// right-hand sides interleaved.
+//
+// With A_l the level-l matrix, d_l its l1-Jacobi scaling and P the
+// piecewise-constant prolongation, the cycle on b_0 is
+//   down (l = 0 .. m-1): y_l = d_l b_l,  r_l = b_l - A_l y_l,  b_{l+1} = P^T r_l
+//   coarsest:            x_m = A_m^-1 b_m
+//   up   (l = m-1 .. 0): x_l = y_l + P x_{l+1} + d_l (r_l - A_l P x_{l+1})
+// which is y_l + P x_{l+1} followed by one l1-Jacobi step on b_l, since
+// b_l - A_l (y_l + P x_{l+1}) = r_l - A_l P x_{l+1}.
+#pragma once
+
+#include "amg.cuh"
+
+namespace mvgd {
+
+// Sum over the 8 lanes of each aggregate (lanes 8g .. 8g+7).
+__device__ __forceinline__ float agg_sum8(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    return v;
+}
+
+// Level-0 matrix-vector product with the operator's FP32 weights:
+// (A x)_i = (sigma - w_0) x_i - sum_s w_s x_{col_s}, with x given by `xv(j)`.
+template <typename XV>
+__device__ __forceinline__ float a0_row(const AmgHeader& H, int64_t r, float xi, XV&& xv) {
+    const int k = H.k, m = k + 1;
+    const float* w = H.lv[0].val + (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
+    const int32_t* c = H.col0 + (r / kSlice) * (int64_t)(kSlice * k) + (r % kSlice);
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int s = 0; s < k; s++) acc = fmaf(w[(s + 1) * kSlice], xv((int64_t)c[s * kSlice]), acc);
+    return ((float)H.sigma - w[0]) * xi - acc;
+}
+
+// Level-l (>= 1) product with the explicit Galerkin matrix; padding slots are
+// (own row, 0), so every lane runs to the slice's widest row.
+template <typename XV>
+__device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, XV&& xv) {
+    const int64_t base = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
+    const int w = Lv.sw[r / kSlice];
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int s = 0; s < w; s++) acc = fmaf(Lv.val[base + s * kSlice], xv((int64_t)Lv.col[base + s * kSlice]), acc);
+    return acc;
+}
+
+// Down step of level l for right-hand side q of the warp's rows.  `b` is the
+// row's own right-hand side (level 0: the Krylov vector, rounded to FP32),
+// `y_of(j)` the pre-smoothed y_l at any row j (already stored: level 0 by the
+// step that formed b_0, level >= 1 by the restriction that formed b_l).
+// Writes r_l, and b_{l+1}, y_{l+1} of the aggregate (its first lane).
+template <typename YOF>
+__device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int64_t r, bool valid, int Q, int q, float b,
+                                          float yi, YOF&& y_of, float* R, float* Bn, float* Yn) {
+    float res = 0.0f;
+    if (valid) {
+        const float ay = (l == 0) ? a0_row(H, r, yi, y_of) : al_row(H.lv[l], r, y_of);
+        res = b - ay;
+        R[r * Q + q] = res;
+    }
+    const float bc = agg_sum8(res);  // rows past the end contribute 0
+    if (valid && (r % kAmgAgg) == 0) {
+        const int64_t I = r / kAmgAgg;
+        Bn[I * Q + q] = bc;
+        if (Yn) Yn[I * Q + q] = H.lv[l + 1].dinv[I] * bc;
+    }
+}
+
+// Up step of level l: x_l = y_l + P x_{l+1} + d_l (r_l - A_l P x_{l+1}).
+template <typename XC>
+__device__ __forceinline__ float vup_row(const AmgHeader& H, int l, int64_t r, int Q, int q, float yi, float ri,
+                                         XC&& xc_of) {
+    const float xc = xc_of(r / kAmgAgg);
+    auto pxc = [&](int64_t j) { return xc_of(j / kAmgAgg); };
+    const float apx = (l == 0) ? a0_row(H, r, xc, pxc) : al_row(H.lv[l], r, pxc);
+    return yi + xc + H.lv[l].dinv[r] * (ri - apx);
+}
+
+// Coarsest solve, one warp per row rho: x[rho] = sum_c Cinv[rho][c] b[c].
+template <typename BOF>
+__device__ __forceinline__ float coarse_row(const AmgHeader& H, int64_t rho, BOF&& b_of) {
+    const int64_t nc = H.nc;
+    const float* row = H.cinv + rho * nc;
+    float acc = 0.0f;
+    for (int64_t c = lane_id(); c < nc; c += kWarp) acc = fmaf(row[c], b_of(c), acc);
+    return warp_sum(acc);
+}
+
+}  // namespace mvgd

@@ -17,7 +17,7 @@ from . import api
 # kernels each stage launches (the C ABI's own launches, not counting memsets/copies)
 KERNELS_KNN = 11          # bbox x2, occupancy, params, count, scan x3, scatter, bucket sort, query
 KERNELS_ASSEMBLE = 1      # + 1 inverse-order kernel with a locality order
-KERNELS_SOLVE = 5         # fill chunks, init states, persistent solver, finish + 2 gathers, 1 scatter with order
+KERNELS_SOLVE = 9         # init: 2 gathers + state; iterate: table, count, solver, exit marks; finish: 2
 
 
 class Pipeline:
@@ -35,13 +35,21 @@ class Pipeline:
         self.order = torch.empty(n, dtype=torch.int32, device=dev) if reorder else None
         self.ws_knn = torch.empty(L.mvgd_knn_workspace_bytes(n, k), dtype=torch.uint8, device=dev)
         self.ws_asm = torch.empty(max(256, L.mvgd_assemble_workspace_bytes(n)), dtype=torch.uint8, device=dev)
-        self.ws_solve = torch.empty(L.mvgd_solve_workspace_bytes(n, k, nrhs, prec), dtype=torch.uint8, device=dev)
+        self.precond = precond
+        solve_bytes = L.mvgd_solve_workspace_bytes(n, k, nrhs, prec, precond)
+        if precond == LB.PRECOND_AMG:  # the hierarchy is built below, outside the solve workspace
+            solve_bytes -= (L.mvgd_amg_workspace_bytes(n, k) + 255) // 256 * 256
+        self.ws_solve = torch.empty(solve_bytes, dtype=torch.uint8, device=dev)
+        # the multigrid hierarchy lives beside the solver workspace and is rebuilt every run
+        self.ws_amg = (torch.empty(L.mvgd_amg_workspace_bytes(n, k), dtype=torch.uint8, device=dev)
+                       if precond == LB.PRECOND_AMG else None)
         col, val, lo = api.ell_alloc(n, k, prec, dev)
         self.op = api.Operator(n, k, prec, col, val, lo, self.order)
         self.op.bad_rows = torch.zeros(1, dtype=torch.int32, device=dev)
         self.u = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
         self.info = torch.zeros(nrhs * C.sizeof(LB.SolveInfo), dtype=torch.uint8, device=dev)
-        self.opts = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond)
+        self.opts = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond,
+                                 api._vp(self.ws_amg))
         self.rule = LB.DeltaRule(api.DELTA_MEAN_NN, delta_m, 1.0)
         # host-side staging for run_host
         self.pts_dev = torch.empty((n, 3), dtype=torch.float64, device=dev)
@@ -49,8 +57,18 @@ class Pipeline:
 
     @property
     def kernels_per_run(self) -> int:
-        return (KERNELS_KNN + KERNELS_ASSEMBLE + (1 if self.reorder else 0) + KERNELS_SOLVE
-                + (3 if self.reorder else 0))
+        k = KERNELS_KNN + KERNELS_ASSEMBLE + (1 if self.reorder else 0) + KERNELS_SOLVE
+        if self.precond == LB.PRECOND_ROWSCALE:
+            k += 1                                   # row scaling
+        if self.precond == LB.PRECOND_AMG:
+            lv = 1
+            m = self.n
+            while m > LB.AMG_COARSEST:
+                m = (m + LB.AMG_AGG - 1) // LB.AMG_AGG
+                lv += 1
+            k += 4 + 2 * (lv - 1)                    # hierarchy set-up
+            k += (lv - 2 if lv > 2 else 0) + 1       # level and coarsest chunk tables
+        return k
 
     def run(self, pts: torch.Tensor, f: torch.Tensor) -> torch.Tensor:
         """Enqueue kNN + assembly + solve on the stream; returns the device info buffer."""
@@ -74,6 +92,8 @@ class Pipeline:
             events[2].record(st)
         with torch.cuda.stream(st):
             self.u.zero_()
+        if self.ws_amg is not None:
+            LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(self.ws_amg), self.ws_amg.numel(), s))
         LB.check("mvgd_solve", L.mvgd_solve(C.byref(c), self.nrhs, 1.0, vp(f), vp(self.u), C.byref(self.opts),
                                              vp(self.info), None, vp(self.ws_solve), self.ws_solve.numel(), s))
         return self.info

@@ -63,14 +63,31 @@ class _Live:
     ws: torch.Tensor
     u: torch.Tensor
     info: torch.Tensor
+    amg: torch.Tensor | None = None
+    opts: LB.SolveOpts | None = None
 
 
-def request_bytes(n: int, k: int, q: int, prec: int) -> int:
+def request_bytes(n: int, k: int, q: int, prec: int, precond: int = 1) -> int:
     """Device bytes one admitted request holds until it retires."""
     L = LB.load()
     ell = sum(L.mvgd_ell_bytes(n, k, prec, w) for w in (LB.ELL_COL, LB.ELL_VAL, LB.ELL_VAL_LO))
-    return (24 * n + 16 * n * q + 4 * n * k + 4 * n + ell + L.mvgd_request_workspace_bytes(n, k, q, prec)
-            + 4 * n + 4096)
+    amg = L.mvgd_amg_workspace_bytes(n, k) if precond == LB.PRECOND_AMG else 0
+    return (24 * n + 16 * n * q + 4 * n * k + 4 * n + ell + L.mvgd_request_workspace_bytes(n, k, q, prec, precond)
+            + amg + 4 * n + 4096)
+
+
+def amg_levels(n: int) -> int:
+    """Levels of the multigrid hierarchy of an n-row operator (the library's rule)."""
+    lv = 1
+    while n > LB.AMG_COARSEST:
+        n = (n + LB.AMG_AGG - 1) // LB.AMG_AGG
+        lv += 1
+    return lv
+
+
+def amg_setup_kernels(n: int) -> int:
+    """Kernels mvgd_amg_setup launches: header, level 0, two per coarser level, dense, inverse."""
+    return 4 + 2 * (amg_levels(n) - 1)
 
 
 class Server:
@@ -82,6 +99,7 @@ class Server:
         self.prec = prec
         self.epoch_iters = epoch_iters
         self.max_active = max_active
+        self.precond = precond
         self.opts = LB.SolveOpts(rtol, maxit, 20000, inner_rtol, 60, precond)
         self.rule = LB.DeltaRule(api.DELTA_MEAN_NN, 6, 1.0)
         L = LB.load()
@@ -119,11 +137,17 @@ class Server:
                 self.launches += 11
                 col, val, lo = api.ell_alloc(n, k, self.prec, self.device)
                 op = api.Operator(n, k, self.prec, col, val, lo, order)
-                ws = torch.empty(L.mvgd_request_workspace_bytes(n, k, q, self.prec), dtype=torch.uint8,
+                ws = torch.empty(L.mvgd_request_workspace_bytes(n, k, q, self.prec, self.precond), dtype=torch.uint8,
                                  device=self.device)
                 u = torch.empty((n, q), dtype=torch.float64, device=self.device)
                 info = torch.zeros(q * C.sizeof(LB.SolveInfo), dtype=torch.uint8, device=self.device)
-                live.append(_Live(r, request_bytes(n, k, q, self.prec), pts, f, nbr, order, op, ws, u, info))
+                amg, opts = None, self.opts
+                if self.precond == LB.PRECOND_AMG:
+                    amg = torch.empty(L.mvgd_amg_workspace_bytes(n, k), dtype=torch.uint8, device=self.device)
+                    opts = LB.SolveOpts(self.opts.rtol, self.opts.maxit, self.opts.inner_maxit, self.opts.inner_rtol,
+                                        self.opts.max_outer, self.precond, C.c_void_p(amg.data_ptr()))
+                live.append(_Live(r, request_bytes(n, k, q, self.prec, self.precond), pts, f, nbr, order, op, ws, u,
+                                  info, amg, opts))
             items = (LB.AssembleItem * len(live))()
             ns = (C.c_int64 * len(live))(*[x.req.n for x in live])
             aws = torch.empty(L.mvgd_assemble_batch_workspace_bytes(ns, len(live)), dtype=torch.uint8,
@@ -135,9 +159,12 @@ class Server:
             self.launches += 1 + len(live) + (len(live) + 47) // 48
             for x in live:
                 c = x.op.cstruct()
+                if x.amg is not None:
+                    LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(x.amg), x.amg.numel(), s))
+                    self.launches += amg_setup_kernels(x.req.n)
                 LB.check("mvgd_request_init", L.mvgd_request_init(vp(x.ws), x.ws.numel(), C.byref(c), x.req.nrhs,
-                                                                   1.0, vp(x.f), None, C.byref(self.opts), s))
-                self.launches += 3
+                                                                   1.0, vp(x.f), None, C.byref(x.opts), s))
+                self.launches += 3 + (1 if self.precond == LB.PRECOND_ROWSCALE else 0)
         return live
 
     # -- one epoch over the active set ---------------------------------------------------
@@ -147,15 +174,17 @@ class Server:
         s = api._stream(self.stream)
         cnt = len(active)
         reqs = (C.c_void_p * cnt)(*[x.ws.data_ptr() for x in active])
-        rows = (C.c_int64 * cnt)(*[x.req.n for x in active])
-        nrhs = (C.c_int32 * cnt)(*[x.req.nrhs for x in active])
-        ks = (C.c_int32 * cnt)(*[x.req.k for x in active])
+        descs = LB.requests([(x.ws, x.req.n, x.req.nrhs, x.req.k) for x in active])
         with torch.cuda.stream(self.stream):
-            LB.check("mvgd_iterate", L.mvgd_iterate(reqs, rows, nrhs, ks, cnt, self.prec, self.epoch_iters, None,
+            LB.check("mvgd_iterate", L.mvgd_iterate(descs, cnt, self.prec, self.precond, self.epoch_iters, None,
                                                      vp(self.ctl_ws), self.ctl_bytes, s))
             LB.check("mvgd_request_poll", L.mvgd_request_poll(reqs, cnt, vp(self.done_dev), s))
             self.done_host[:cnt].copy_(self.done_dev[:cnt], non_blocking=True)
-        self.launches += 4 + (cnt + 255) // 256 * 2
+        groups = (cnt + 255) // 256
+        tables = 1
+        if self.precond == LB.PRECOND_AMG:
+            tables += max(amg_levels(x.req.n) - 1 for x in active)  # levels 1 .. mlev-1, and the coarsest
+        self.launches += groups * tables + 3 + groups              # tables, count, solver, exit marks, poll
         self.stream.synchronize()
         self.epochs += 1
         return [i for i in range(cnt) if int(self.done_host[i]) != 0]

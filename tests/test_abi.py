@@ -53,7 +53,14 @@ def test_host_side_queries(lib_path):
     assert L.mvgd_ell_bytes(n, k, LB.FP64, LB.ELL_VAL) == 1024 * 21 * 8
     assert L.mvgd_ell_bytes(n, k, LB.FP32_REFINE, LB.ELL_VAL_LO) == 1024 * 21 * 4
     assert L.mvgd_ell_bytes(n, k, LB.FP64, LB.ELL_VAL_LO) == 0
-    assert L.mvgd_solve_workspace_bytes(n, k, 2, LB.FP32_REFINE) > 9 * 4 * 2 * n
+    assert L.mvgd_solve_workspace_bytes(n, k, 2, LB.FP32_REFINE, 1) > 9 * 4 * 2 * n
+    # the multigrid hierarchy and its per-level vectors come on top
+    assert L.mvgd_solve_workspace_bytes(n, k, 2, LB.FP32_REFINE, 2) > (L.mvgd_solve_workspace_bytes(
+        n, k, 2, LB.FP32_REFINE, 1) + L.mvgd_amg_workspace_bytes(n, k))
+    assert L.mvgd_amg_workspace_bytes(n, k) > 4 * (k + 1) * n
+    assert L.mvgd_amg_workspace_bytes(n, 4) == 0 and L.mvgd_amg_workspace_bytes(0, k) == 0
+    assert L.mvgd_amg_apply_workspace_bytes(n, 2) >= 2 * 4 * 2 * n
+    assert L.mvgd_request_workspace_bytes(n, k, 1, LB.FP64, 3) == 0
 
 
 def test_argument_errors_are_reported_before_any_launch(lib_path):
@@ -81,3 +88,14 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
     info = (LB.SolveInfo * 1)()
     assert L.mvgd_solve(C.byref(e), 1, 1.0, C.c_void_p(256), C.c_void_p(512), C.byref(opts),
                         C.cast(info, C.c_void_p), None, C.c_void_p(1024), 1 << 30, None) == LB.EINVAL  # rtol 0
+    # multigrid: bad K, misaligned workspace, too small a workspace; an iterate with an unknown preconditioner
+    e5 = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
+    assert L.mvgd_amg_setup(C.byref(e5), 1.0, C.c_void_p(1024), 1 << 30, None) == LB.EINVAL
+    assert L.mvgd_amg_setup(C.byref(e), 1.0, C.c_void_p(1025), 1 << 30, None) == LB.EINVAL
+    assert L.mvgd_amg_setup(C.byref(e), 1.0, C.c_void_p(1024), 64, None) == LB.EWORKSPACE
+    reqs = LB.requests([(256, 100, 1, 10)])
+    assert L.mvgd_iterate(reqs, 1, LB.FP64, 3, 10, None, C.c_void_p(1024), 1 << 20, None) == LB.EINVAL
+    assert L.mvgd_iterate(reqs, 1, LB.FP64, 0, 10, None, C.c_void_p(1024), 16, None) == LB.EWORKSPACE
+    amg_opts = LB.SolveOpts(1e-8, 10, 10, 1e-5, 5, 2, C.c_void_p(0))
+    assert L.mvgd_request_init(C.c_void_p(1024), 1 << 30, C.byref(e), 1, 1.0, C.c_void_p(256), None,
+                               C.byref(amg_opts), None) == LB.EINVAL  # precond 2 needs a hierarchy
