@@ -343,7 +343,7 @@ def trace_read(max_entries: int = 1 << 16) -> list:
     prev = None
     for i in range(n):
         code, t = buf[i] >> 48, buf[i] & ((1 << 48) - 1)
-        if code >= 0x100:
+        if code >= 0x1000:
             side, kind, lvl = (code >> 8) & 1, (code >> 4) & 15, code & 15
             name = f"V{'ps'[side]}:{('down', 'coarse', 'up')[kind]}{'' if kind == 1 else lvl}"
         else:

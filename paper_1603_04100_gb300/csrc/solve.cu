@@ -125,7 +125,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-// step code: Krylov phase ph (0..4), or 0x100 | side << 8 | kind << 4 | level for a V-cycle step
+// step code: Krylov phase ph (0..4), or 0x1000 | side << 8 | kind << 4 | level for a V-cycle step
 __device__ __forceinline__ void trace_step(const Ctl& ctl, unsigned code) {
     if (!ctl.trace || blockIdx.x != 0 || threadIdx.x != 0) return;
     const unsigned i = g_trace_n;
@@ -914,7 +914,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             }
         }
         const bool ok = grid_sync(ctl.bar, ctl.err, ctl.limit);
-        trace_step(ctl, 0x100u | ((unsigned)side << 8) | ((unsigned)kind << 4) | (unsigned)l);
+        trace_step(ctl, 0x1000u | ((unsigned)side << 8) | ((unsigned)kind << 4) | (unsigned)l);
         return ok;
     };
     auto vcycle = [&](int side) -> bool {
