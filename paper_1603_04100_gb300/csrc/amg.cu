@@ -50,6 +50,7 @@ AmgLayout amg_layout(void* ws, int64_t n, int k) {
             L.val64 = cv.take<double>(np * kAmgStride);
             L.cnt = cv.take<int32_t>(np);
             L.sw = cv.take<int32_t>(np / kSlice);
+            L.rs = cv.take<float>(np);
         }
         L.dinv = cv.take<float>(np);
     }
@@ -88,8 +89,10 @@ __global__ void k_amg_level0(const AmgHeader* __restrict__ Hp, OpView O) {
         const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
         double l1 = 0.0;
         for (int s = 0; s < m; s++) {
-            const double w = op_weight(O, vb + (int64_t)s * kSlice);
-            H.lv[0].val[vb + (int64_t)s * kSlice] = (float)w;
+            const int64_t idx = vb + (int64_t)s * kSlice;
+            const double w = op_weight(O, idx);
+            // FP64 weights round to nearest; the mixed format's hi is already that rounding
+            H.lv[0].val[idx] = O.prec == MVGD_FP64 ? (float)w : static_cast<const float*>(O.val)[idx];
             l1 += s == 0 ? fabs(sigma - w) : fabs(w);
         }
         H.lv[0].dinv[r] = l1 > 0.0 ? (float)(1.0 / l1) : 1.0f;
@@ -140,7 +143,7 @@ __global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
         }
         const int64_t ob = (I / kSlice) * (int64_t)(kSlice * kAmgStride) + (I % kSlice);
         int out = 0;
-        double l1 = 0.0;
+        double l1 = 0.0, rsum = 0.0;
         while (true) {
             int mine = INT_MAX;
 #pragma unroll
@@ -163,6 +166,7 @@ __global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
                 Cl.val[ob + (int64_t)out * kSlice] = (float)tot;
             }
             l1 += fabs(tot);
+            rsum += tot;
             out++;
         }
         if (lane == 0) {
@@ -171,6 +175,7 @@ __global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
             const int c = min(out, kAmgStride);
             Cl.cnt[I] = c;
             Cl.dinv[I] = l1 > 0.0 ? (float)(1.0 / l1) : 1.0f;
+            Cl.rs[I] = (float)rsum;
         }
         // padding: (own row, 0) up to the full stride, so slice loops need no bounds
         for (int s = min(out, kAmgStride) + lane; s < kAmgStride; s += kWarp) {
@@ -357,7 +362,8 @@ __global__ void k_vdown(const AmgHeader* __restrict__ Hp, int l, const double* _
             const float bi = valid ? (l == 0 ? (float)b0[r * Q + q] : V.b[l][r * Q + q]) : 0.0f;
             const float yi = valid ? Y[r * Q + q] : 0.0f;
             vdown_row(H, l, r, valid, Q, q, bi, yi, [&](int64_t j) { return Y[j * Q + q]; }, V.r[l], V.b[l + 1],
-                      last ? nullptr : V.y[l + 1]);
+                      last ? nullptr : V.y[l + 1],
+                      [&](float xi, auto&& xv) { return a0_row(H, r, xi, xv); });
         }
     }
 }
@@ -386,7 +392,8 @@ __global__ void k_vup(const AmgHeader* __restrict__ Hp, int l, double* x0, int Q
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nl; r += (int64_t)gridDim.x * blockDim.x) {
         for (int q = 0; q < Q; q++) {
             const float x = vup_row(H, l, r, Q, q, V.y[l][r * Q + q], V.r[l][r * Q + q],
-                                    [&](int64_t J) { return Xc[J * Q + q]; });
+                                    [&](int64_t J) { return Xc[J * Q + q]; },
+                                    [&](float xi, auto&& xv) { return a0_row(H, r, xi, xv); });
             if (l == 0) x0[r * Q + q] = (double)x;
             else V.x[l][r * Q + q] = x;
         }

@@ -24,6 +24,7 @@ struct AmgLevel {
     int32_t* cnt;    // level >= 1: [n] entries per row
     int32_t* sw;     // level >= 1: [n_pad / 32] widest row of each slice
     float* dinv;     // [n] 1 / sum_j |a_ij|  (l1-Jacobi)
+    float* rs;       // level >= 1: [n] row sums sum_j a_ij (FP64 sums, rounded once)
 };
 
 struct AmgHeader {

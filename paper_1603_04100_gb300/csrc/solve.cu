@@ -28,6 +28,7 @@
 //   INNER    BiCGSTAB until the recursive residual meets the restart target;
 //            a diverging FP32 inner solve is abandoned and its correction dropped
 //   DONE
+#include <stdlib.h>
 #include <string.h>
 
 #include <type_traits>
@@ -207,24 +208,83 @@ __device__ __forceinline__ void c_row_f64(const Prob& P, int64_t r, const RhsSta
     }
 }
 
-// Starts the copy of one 32-row slice of the operator -- its k column slots
+// Per-warp staging of operator slices.  A slice -- 32 rows' k column slots
 // and k+1 weight slots, each 32 consecutive words in the sliced layout, so two
-// contiguous runs -- into the warp's shared-memory buffer: one bulk
-// asynchronous copy per run, issued by lane 0, completing on the warp's
-// mbarrier.  The evict-first hint keeps the small, reused Krylov vectors in L2
-// while the operator streams past.
-template <typename VT>
-__device__ __forceinline__ void stage_slice(const Prob& P, int64_t slice, int* colS, VT* valS, uint64_t* bar,
-                                            uint64_t pol) {
-    const int k = P.k, m = k + 1;
-    __syncwarp();  // every lane has consumed the previous slice (its values fed the row sums)
-    if (lane_id() == 0) {
-        const uint32_t cb = (uint32_t)(kSlice * k * sizeof(int)), vb = (uint32_t)(kSlice * m * sizeof(VT));
-        mbar_expect_tx(bar, cb + vb);
-        bulk_g2s(colS, P.col + slice * (int64_t)(kSlice * k), cb, bar, pol);
-        bulk_g2s(valS, static_cast<const VT*>(P.val) + slice * (int64_t)(kSlice * m), vb, bar, pol);
+// contiguous runs -- arrives in the warp's shared memory by two bulk
+// asynchronous copies issued by lane 0 and completing on one of the warp's
+// mbarriers.  With two buffers the slice of the warp's next tile is requested
+// before the current one is used, so the operator keeps streaming while the
+// warp gathers and reduces.  The evict-first hint keeps the small, reused
+// Krylov vectors in L2 while the operator streams past.
+struct Stager {
+    unsigned char* base;  // this warp's buffers
+    uint32_t bytes;       // one buffer
+    uint32_t val_off;     // where the weights start inside a buffer
+    uint64_t* bar;        // [2] this warp's mbarriers
+    uint64_t pol;
+    uint32_t parity;      // bit b: parity of buffer b's next completion
+    uint32_t busy;        // bit b: a copy into buffer b has not been waited for
+    int nbuf;
+    int next_c;           // tile whose slice was requested ahead (-1: none), in buffer next_b
+    int next_b;
+    bool ok;              // false once a copy missed its wait: nothing more is issued
+
+    __device__ int* col(int b) const { return reinterpret_cast<int*>(base + b * bytes); }
+    __device__ const void* val(int b) const { return base + b * bytes + val_off; }
+
+    __device__ void issue(int b, const int32_t* colsrc, const void* valsrc, int esize, int k, int64_t slice) {
+        __syncwarp();  // every lane has consumed what buffer b held
+        busy |= 1u << b;
+        if (lane_id() == 0) {
+            const uint32_t cb = (uint32_t)(kSlice * k * 4), vb = (uint32_t)(kSlice * (k + 1) * esize);
+            mbar_expect_tx(&bar[b], cb + vb);
+            bulk_g2s(col(b), colsrc + slice * (int64_t)(kSlice * k), cb, &bar[b], pol);
+            bulk_g2s(base + b * bytes + val_off,
+                     static_cast<const char*>(valsrc) + slice * (int64_t)(kSlice * (k + 1)) * esize, vb, &bar[b],
+                     pol);
+        }
     }
-}
+
+    // The buffer holding tile c's slice: requested now unless it was requested
+    // ahead; then, with two buffers, requests tile c2's slice ahead (c2 < 0: none).
+    __device__ int acquire(int c, int64_t slice, int c2, int64_t slice2, const int32_t* colsrc, const void* valsrc,
+                           int esize, int k, int* err) {
+        if (next_c >= 0 && next_c != c) {  // a slice requested ahead for a tile not taken: let it land first
+            wait(next_b, err);
+            next_c = -1;
+        }
+        int b;
+        if (next_c == c) {
+            b = next_b;
+        } else {
+            b = (busy & 1u) ? 1 : 0;
+            issue(b, colsrc, valsrc, esize, k, slice);
+        }
+        next_c = -1;
+        if (nbuf == 2 && c2 >= 0) {
+            next_b = b ^ 1;
+            next_c = c2;
+            issue(next_b, colsrc, valsrc, esize, k, slice2);
+        }
+        return b;
+    }
+
+    // Warp-collective bounded wait for buffer b.
+    __device__ bool wait(int b, int* err) {
+        const bool landed = mbar_wait(&bar[b], (parity >> b) & 1u, kStageWaitLimit);
+        parity ^= 1u << b;
+        busy &= ~(1u << b);
+        ok = __all_sync(0xffffffffu, landed) && ok;
+        if (!ok && lane_id() == 0) atomicCAS(err, 0, (int)MVGD_ETIMEOUT);
+        return ok;
+    }
+
+    // Before the block's shared memory goes away: bounded waits for copies in flight.
+    __device__ void drain() {
+        for (int b = 0; b < 2; b++)
+            if (busy & (1u << b)) mbar_wait(&bar[b], (parity >> b) & 1u, kStageWaitLimit);
+    }
+};
 
 // A / B for INNER right-hand sides: one operator application each, reading
 // the row's columns and weights from the warp's staged slice.  Called by every
@@ -698,9 +758,20 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
 
 enum VStep : int { V_DOWN = 0, V_COARSE = 1, V_UP = 2 };
 
+// The tile this block takes after tile c in a step over table T, if it is
+// request ri's and this warp's slice of it holds rows (its slice in *slice2);
+// else -1.  Such a tile is staged exactly like tile c, so its slice can be
+// requested ahead.
+__device__ __forceinline__ int next_tile(const ChunkTable& T, int c, int ri, int64_t nrows, int wid, int64_t& slice2) {
+    const int c2 = c + (int)gridDim.x;
+    if (c2 >= T.nchunks || T.chunk_req[c2] != ri) return -1;
+    slice2 = (int64_t)(c2 - T.chunk_base[ri]) * (kCh / kSlice) + wid;
+    return slice2 * kSlice < nrows ? c2 : -1;
+}
+
 template <bool MIXED, int QT, bool AMG>
 __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
-    k_solve(ReqTable tab, Ctl ctl, int iter_budget, int kmax) {
+    k_solve(ReqTable tab, Ctl ctl, int iter_budget, int kmax, int nbuf) {
     using VT = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char stage_smem[];
     __shared__ RhsState S[QT];
@@ -708,29 +779,28 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     __shared__ double fin[kThreads / 32][kChan * QT];
     __shared__ double tot[kChan * QT];
     __shared__ int last;
-    __shared__ __align__(8) uint64_t stage_bar[kThreads / 32];
+    __shared__ __align__(8) uint64_t stage_bar[kThreads / 32][2];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    // this warp's slice buffer: kmax column slots, then kmax + 1 weight slots
-    const size_t warp_bytes = stage_bytes_per_warp<VT>(kmax);
-    int* colS = reinterpret_cast<int*>(stage_smem + wid * warp_bytes);
-    VT* valS = reinterpret_cast<VT*>(stage_smem + wid * warp_bytes + (size_t)kSlice * kmax * sizeof(int));
-    uint64_t* bar = &stage_bar[wid];
-    uint64_t pol = 0;
+    // this warp's nbuf slice buffers: kmax column slots, then kmax + 1 weight slots each
+    Stager st;
+    st.bytes = (uint32_t)stage_bytes_per_warp<VT>(kmax);
+    st.val_off = (uint32_t)(kSlice * kmax * sizeof(int));
+    st.base = stage_smem + (size_t)wid * nbuf * st.bytes;
+    st.bar = stage_bar[wid];
+    st.pol = 0;
+    st.parity = 0;
+    st.busy = 0;
+    st.nbuf = nbuf;
+    st.next_c = -1;
+    st.next_b = 0;
+    st.ok = true;
     if (lane == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&st.bar[0], 1);
+        mbar_init(&st.bar[1], 1);
         fence_mbar_init();
-        pol = l2_evict_first_policy();
+        st.pol = l2_evict_first_policy();
     }
     __syncthreads();
-    uint32_t parity = 0;   // phase of the warp's mbarrier that the next copy completes
-    bool stage_ok = true;  // false once a copy failed to land in time: no more copies are issued
-    auto landed = [&]() {
-        const bool ok = mbar_wait(bar, parity, kStageWaitLimit);
-        parity ^= 1u;
-        stage_ok = __all_sync(0xffffffffu, ok);
-        if (!stage_ok && lane == 0) atomicCAS(ctl.err, 0, (int)MVGD_ETIMEOUT);
-        return stage_ok;
-    };
 
     bool inner[QT], restart[QT];
     bool any_inner = false, any_restart = false, all_done = true;
@@ -797,9 +867,14 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
 #pragma unroll
                 for (int q = 0; q < QT; q++) { af[ch][q].hi = 0.0f; af[ch][q].lo = 0.0f; ad[ch][q] = 0.0; }
             // warp-uniform: lane 0 stages the whole slice and every lane waits for it
-            const bool staged = (ph == P_A || ph == P_B) && any_inner && slice * kSlice < P.n && stage_ok;
+            const bool staged = (ph == P_A || ph == P_B) && any_inner && slice * kSlice < P.n && st.ok;
             if (staged) {
-                stage_slice<VT>(P, slice, colS, valS, bar, pol);
+                int64_t slice2 = 0;
+                const int cn = next_tile(tab.fine, c, ri, P.n, wid, slice2);
+                const int b = st.acquire(c, slice, cn, slice2, P.col, P.val, (int)sizeof(VT), P.k, ctl.err);
+                const int* colS = st.col(b);
+                const VT* valS = static_cast<const VT*>(st.val(b));
+                auto landed = [&]() { return st.wait(b, ctl.err); };
                 if (AMG) amg_spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, af, ad, colS, valS, landed);
                 else spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, c1, c2, af, ad, colS, valS, landed);
             }
@@ -889,25 +964,56 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             const int64_t r = (int64_t)lc * kCh + tid;
             if (r - lane >= nl) continue;  // whole warps past the level's end
             const bool valid = r < nl;
+            // level 0 reads the operator's slice from a staged buffer, like A and B
+            const int* colS = nullptr;
+            const float* w0S = nullptr;
+            int b = 0;
+            if (l == 0) {
+                if (!st.ok) continue;
+                const int64_t slice = (int64_t)lc * (kCh / kSlice) + wid;
+                int64_t slice2 = 0;
+                const int cn = next_tile(tab.fine, c, ri, nl, wid, slice2);
+                b = st.acquire(c, slice, cn, slice2, P.col, H.lv[0].val, 4, P.k, ctl.err);
+                colS = st.col(b);
+                w0S = static_cast<const float*>(st.val(b));
+            }
+            const float sig = (float)P.sigma;
+            const int k = P.k;
+            auto a0 = [&](float xi, auto&& xv) {
+                return l == 0 ? a0_row_staged(colS, w0S, lane, k, sig, xi, xv) : a0_row(H, r, xi, xv);
+            };
             if (kind == V_DOWN) {
                 float* Yn = (l + 1 < m) ? P.vy[l + 1] : nullptr;
+                const float* Y = P.vy[l];
+                float bi[QT], yi[QT];
+#pragma unroll
+                for (int q = 0; q < QT; q++) {  // the row's own values, loaded while the slice lands
+                    bi[q] = (valid && inner[q]) ? (l == 0 ? (float)B0[r * Q + q] : P.vb[l][r * Q + q]) : 0.0f;
+                    yi[q] = (valid && inner[q]) ? Y[r * Q + q] : 0.0f;
+                }
+                if (l == 0 && !st.wait(b, ctl.err)) continue;
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
                     if (!inner[q]) continue;
-                    const float* Y = P.vy[l];
-                    const float bi = valid ? (l == 0 ? (float)B0[r * Q + q] : P.vb[l][r * Q + q]) : 0.0f;
-                    const float yi = valid ? Y[r * Q + q] : 0.0f;
-                    vdown_row(H, l, r, valid, Q, q, bi, yi, [&](int64_t j) { return Y[j * Q + q]; }, P.vr[l],
-                              P.vb[l + 1], Yn);
+                    vdown_row(H, l, r, valid, Q, q, bi[q], yi[q], [&](int64_t j) { return Y[j * Q + q]; }, P.vr[l],
+                              P.vb[l + 1], Yn, a0);
                 }
-            } else if (valid) {
+            } else {
                 const float* Xc = P.vx[l + 1];
+                float yi[QT], rr[QT];
+#pragma unroll
+                for (int q = 0; q < QT; q++) {
+                    yi[q] = (valid && inner[q]) ? P.vy[l][r * Q + q] : 0.0f;
+                    rr[q] = (valid && inner[q]) ? P.vr[l][r * Q + q] : 0.0f;
+                }
+                if (l == 0 && !st.wait(b, ctl.err)) continue;
+                if (!valid) continue;
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
                     if (!inner[q]) continue;
                     const int64_t e = r * Q + q;
-                    const float x = vup_row(H, l, r, Q, q, P.vy[l][e], P.vr[l][e],
-                                            [&](int64_t J) { return Xc[J * Q + q]; });
+                    const float x = vup_row(H, l, r, Q, q, yi[q], rr[q], [&](int64_t J) { return Xc[J * Q + q]; },
+                                            a0);
                     if (l == 0) X0[e] = (VT)x;
                     else P.vx[l][e] = x;
                 }
@@ -943,9 +1049,9 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         if (!ok) break;  // error exit, after the drain below
         if (*(volatile int*)ctl.active == 0 || *(volatile int*)ctl.stop != 0) break;
     }
-    // a copy that missed its wait may still be landing: give it one more bounded
-    // wait before the block's shared memory is released
-    if (!stage_ok) mbar_wait(bar, parity ^ 1u, kStageWaitLimit);
+    // copies still landing (a missed wait): bounded waits before the block's
+    // shared memory is released
+    st.drain();
 }
 
 // ------------------------------------------------------------------------------
@@ -1193,11 +1299,25 @@ __global__ void k_poll(TableArgs A, int32_t* done) {
     }
 }
 
+// Slice buffers per warp.  One: a second buffer (the next tile's slice
+// requested ahead) costs a resident block per SM, and on GB300 at 1M rows,
+// K = 20, three single-buffered blocks ran the FP32 multigrid solve 8 %
+// faster than two double-buffered ones (every step that is not a product
+// loses the third block's latency hiding).  MVGD_STAGE_BUFFERS=2 selects two.
+template <typename VT>
+int stage_buffers(int kmax) {
+    const char* e = getenv("MVGD_STAGE_BUFFERS");
+    if (e && e[0] == '2' && e[1] == 0 && 2 * stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp) <= (112u << 10))
+        return 2;
+    return 1;
+}
+
 template <bool MIXED, int QT, bool AMG>
 mvgd_status launch_solve(const ReqTable& tab, Ctl ctl, int budget, int kmax, cudaStream_t s) {
     using VT = typename std::conditional<MIXED, float, double>::type;
     auto fn = k_solve<MIXED, QT, AMG>;
-    const size_t smem = stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp);
+    int nbuf = stage_buffers<VT>(kmax);
+    const size_t smem = stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp) * nbuf;
     int dev = 0, sms = 0, per_sm = 0;
     MVGD_CUDA_TRY(cudaGetDevice(&dev));
     MVGD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1207,7 +1327,7 @@ mvgd_status launch_solve(const ReqTable& tab, Ctl ctl, int budget, int kmax, cud
     int grid = sms * per_sm;
     if (grid > tab.fine.nchunks) grid = tab.fine.nchunks;
     ReqTable t = tab;
-    void* args[] = {(void*)&t, (void*)&ctl, (void*)&budget, (void*)&kmax};
+    void* args[] = {(void*)&t, (void*)&ctl, (void*)&budget, (void*)&kmax, (void*)&nbuf};
     MVGD_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)fn, dim3(grid), dim3(kThreads), args, smem, s));
     return MVGD_OK;
 }

@@ -26,8 +26,18 @@ __device__ __forceinline__ float agg_sum8(float v) {
     return v;
 }
 
-// Level-0 matrix-vector product with the operator's FP32 weights:
-// (A x)_i = (sigma - w_0) x_i - sum_s w_s x_{col_s}, with x given by `xv(j)`.
+// Every product below is taken in difference form, sum_j a_ij (x_j - x_i) +
+// (sum_j a_ij) x_i, with the row sum exact: rows of L sum to zero, so level 0
+// is sigma x_i - sum_s w_s (x_j - x_i), and a Galerkin row sums to sigma times
+// its aggregate's size.  In FP32 the smooth components of a residual b - A y
+// -- the ones the coarse levels exist to remove -- are tiny differences of
+// terms of size h^-2 |y|; summed in the standard form they lose about
+// h^-2 / lambda_smooth times the FP32 rounding (at 1M points, ~1e-3
+// relative), which made the cycle a poor, slightly nonlinear preconditioner
+// (BiCGSTAB needed 457 iterations in an FP32 emulation, 195 with an FP64
+// cycle); in difference form the FP32 cycle stays within a few % of FP64.
+
+// Level-0 product with the operator's FP32 weights, x given by `xv(j)`.
 template <typename XV>
 __device__ __forceinline__ float a0_row(const AmgHeader& H, int64_t r, float xi, XV&& xv) {
     const int k = H.k, m = k + 1;
@@ -35,20 +45,33 @@ __device__ __forceinline__ float a0_row(const AmgHeader& H, int64_t r, float xi,
     const int32_t* c = H.col0 + (r / kSlice) * (int64_t)(kSlice * k) + (r % kSlice);
     float acc = 0.0f;
 #pragma unroll 4
-    for (int s = 0; s < k; s++) acc = fmaf(w[(s + 1) * kSlice], xv((int64_t)c[s * kSlice]), acc);
-    return ((float)H.sigma - w[0]) * xi - acc;
+    for (int s = 0; s < k; s++) acc = fmaf(w[(s + 1) * kSlice], xv((int64_t)c[s * kSlice]) - xi, acc);
+    return (float)H.sigma * xi - acc;
+}
+
+// The same product from a staged slice: colS [k][32] columns, w [k+1][32]
+// weights (slot 0 = the row itself), lane = the row's place in its slice.
+template <typename XV>
+__device__ __forceinline__ float a0_row_staged(const int* colS, const float* w, int lane, int k, float sigma, float xi,
+                                               XV&& xv) {
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int s = 0; s < k; s++)
+        acc = fmaf(w[(s + 1) * kSlice + lane], xv((int64_t)colS[s * kSlice + lane]) - xi, acc);
+    return sigma * xi - acc;
 }
 
 // Level-l (>= 1) product with the explicit Galerkin matrix; padding slots are
 // (own row, 0), so every lane runs to the slice's widest row.
 template <typename XV>
-__device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, XV&& xv) {
+__device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, float xi, XV&& xv) {
     const int64_t base = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
     const int w = Lv.sw[r / kSlice];
     float acc = 0.0f;
 #pragma unroll 4
-    for (int s = 0; s < w; s++) acc = fmaf(Lv.val[base + s * kSlice], xv((int64_t)Lv.col[base + s * kSlice]), acc);
-    return acc;
+    for (int s = 0; s < w; s++)
+        acc = fmaf(Lv.val[base + s * kSlice], xv((int64_t)Lv.col[base + s * kSlice]) - xi, acc);
+    return fmaf(Lv.rs[r], xi, acc);
 }
 
 // Down step of level l for right-hand side q of the warp's rows.  `b` is the
@@ -56,12 +79,13 @@ __device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, XV&& xv) 
 // `y_of(j)` the pre-smoothed y_l at any row j (already stored: level 0 by the
 // step that formed b_0, level >= 1 by the restriction that formed b_l).
 // Writes r_l, and b_{l+1}, y_{l+1} of the aggregate (its first lane).
-template <typename YOF>
+// `a0(xi, xv)` is the level-0 product (from global memory or a staged slice).
+template <typename YOF, typename A0>
 __device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int64_t r, bool valid, int Q, int q, float b,
-                                          float yi, YOF&& y_of, float* R, float* Bn, float* Yn) {
+                                          float yi, YOF&& y_of, float* R, float* Bn, float* Yn, A0&& a0) {
     float res = 0.0f;
     if (valid) {
-        const float ay = (l == 0) ? a0_row(H, r, yi, y_of) : al_row(H.lv[l], r, y_of);
+        const float ay = (l == 0) ? a0(yi, y_of) : al_row(H.lv[l], r, yi, y_of);
         res = b - ay;
         R[r * Q + q] = res;
     }
@@ -74,12 +98,12 @@ __device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int64_t r, 
 }
 
 // Up step of level l: x_l = y_l + P x_{l+1} + d_l (r_l - A_l P x_{l+1}).
-template <typename XC>
+template <typename XC, typename A0>
 __device__ __forceinline__ float vup_row(const AmgHeader& H, int l, int64_t r, int Q, int q, float yi, float ri,
-                                         XC&& xc_of) {
+                                         XC&& xc_of, A0&& a0) {
     const float xc = xc_of(r / kAmgAgg);
     auto pxc = [&](int64_t j) { return xc_of(j / kAmgAgg); };
-    const float apx = (l == 0) ? a0_row(H, r, xc, pxc) : al_row(H.lv[l], r, pxc);
+    const float apx = (l == 0) ? a0(xc, pxc) : al_row(H.lv[l], r, xc, pxc);
     return yi + xc + H.lv[l].dinv[r] * (ri - apx);
 }
 
