@@ -775,7 +775,12 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     using VT = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char stage_smem[];
     __shared__ RhsState S[QT];
-    __shared__ double red[2][kThreads / 32][kChan * QT];
+    // per-warp partials of the block's pending tiles, summed into tile partials
+    // (in warp order) only when kRedTiles are pending or the request changes:
+    // the warps of a block do not wait for each other tile by tile
+    constexpr int kRedTiles = QT <= 2 ? 16 : (QT == 4 ? 8 : 4);
+    __shared__ double red[kRedTiles][kThreads / 32][kChan * QT];
+    __shared__ int red_lc[kRedTiles];
     __shared__ double fin[kThreads / 32][kChan * QT];
     __shared__ double tot[kChan * QT];
     __shared__ int last;
@@ -843,13 +848,28 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     auto fine_phase = [&](int ph) -> bool {
         const bool reduce = ph == P_A || ph == P_B || ph == P_C;
         const int slot = red_slot(ph);
-        int cur = -1, tiles = 0, rb = 0;
+        int cur = -1, tiles = 0, nred = 0;
+        // tile partials of the pending tiles of request P: each the sum of its 8 warp partials in order
+        auto flush = [&](const Prob& P) {
+            __syncthreads();
+            for (int e = tid; e < nred * kChan * QT; e += kThreads) {
+                const int t = e / (kChan * QT), j = e % (kChan * QT);
+                double v = 0.0;
+                for (int w = 0; w < kThreads / 32; w++) v += red[t][w][j];
+                const int ch = j / QT, q = j % QT;
+                if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + red_lc[t]) * P.Q + q] = v;
+            }
+            __syncthreads();
+            nred = 0;
+        };
         for (int c = blockIdx.x;; c += gridDim.x) {
             const int ri = c < tab.fine.nchunks ? tab.fine.chunk_req[c] : -1;
             if (ri != cur) {
                 // leaving request `cur`: publish this block's tiles of it
-                if (cur >= 0 && reduce && tiles > 0)
+                if (cur >= 0 && reduce && tiles > 0) {
+                    flush(*tab.prob[cur]);
                     arrive_and_finalize<MIXED, QT>(*tab.prob[cur], ph, slot, tiles, S, fin, tot, &last, ctl);
+                }
                 if (ri < 0) break;
                 cur = ri;
                 tiles = 0;
@@ -897,24 +917,19 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             }
             if (!reduce) continue;
             // tile partials in a fixed order: FP32 partials within the warp in FP32,
-            // then the 8 warps in order; `red` alternates so one barrier per tile suffices
+            // then (at the next flush) the 8 warps in order
 #pragma unroll
             for (int ch = 0; ch < kChan; ch++)
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
                     double v = f2_to_double(warp_sum_f2(af[ch][q]));
                     if (any_restart || !MIXED) v += warp_sum(ad[ch][q]);
-                    if (lane == 0) red[rb][wid][ch * QT + q] = v;
+                    if (lane == 0) red[nred][wid][ch * QT + q] = v;
                 }
-            __syncthreads();
-            if (tid < kChan * QT) {
-                double v = 0.0;
-                for (int w = 0; w < kThreads / 32; w++) v += red[rb][w][tid];
-                const int ch = tid / QT, q = tid % QT;
-                if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + lc) * P.Q + q] = v;
-            }
-            rb ^= 1;
+            if (tid == 0) red_lc[nred] = lc;
+            nred++;
             tiles++;
+            if (nred == kRedTiles) flush(P);
         }
         // the stop word is written only before the last barrier of an iteration and
         // read only after it, so every block takes the same exit decision
