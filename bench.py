@@ -29,6 +29,8 @@ import tempfile
 import time
 from pathlib import Path
 
+import numpy as np
+
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
@@ -48,6 +50,11 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--workload", choices=["sphere1m", "batched", "served"], default="sphere1m",
+                    help="sphere1m: the headline (1M random sphere); batched: 256 uneven clouds in one batch; "
+                         "served: a Poisson request trace through the serving loop")
+    ap.add_argument("--requests", type=int, default=200, help="served: requests taken from the trace")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: arrival rate (requests/s)")
     ap.add_argument("--paths", default="fp32_refine+amg,fp64+amg,fp32_refine,fp64",
                     help="comma list of <precision>[+amg] paths to time (the fastest is the headline)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
@@ -150,6 +157,40 @@ def solver_bytes_per_row(k: int, mixed: bool, iters: int, restarts: int, amg_coa
     return iters * (24 * k + 160) + restarts * (12 * k + 96)
 
 
+def spmv_roofline(results, n, k, flush, stream, peak, peak_kind, reps: int = 20):
+    """mvgd_spmv timed alone: y = sigma x - L x, one RHS, per launch (CUDA events on the
+    launching stream, L2 flushed before each launch).  Algorithmic bytes per row:
+    FP32 difference form col 4k + val 4k (the self weight is implied) + x_i + y_i = 8k + 8;
+    FP64 col 4k + val 8(k+1) + x_i + y_i = 12k + 24 (neighbour gathers hit L2)."""
+    import torch
+    from paper_1603_04100_gb300 import api
+    out = {}
+    for nm, mode, per_row in (("fp32_difference", api.SPMV_F32, 8 * k + 8), ("fp64", api.SPMV_F64, 12 * k + 24)):
+        src = next((r for r in results.values() if (r["mixed"] if mode == api.SPMV_F32 else not r["mixed"])), None)
+        if src is None:
+            continue
+        op = src["pipe"].op
+        dt = torch.float32 if mode == api.SPMV_F32 else torch.float64
+        x = torch.linspace(-1.0, 1.0, n, device=flush.device, dtype=dt)
+        y = torch.empty_like(x)
+        ms = []
+        with torch.cuda.stream(stream):
+            for i in range(reps + 3):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                api.spmv(op, x, mode=mode, y=y, stream=stream)
+                e1.record(stream)
+                if i >= 3:
+                    ms.append((e0, e1))
+        stream.synchronize()
+        t = statistics.median(a.elapsed_time(b) for a, b in ms)
+        gbs = per_row * n / (t * 1e-3) / 1e9
+        out[nm] = {"us": t * 1e3, "bytes_per_row": per_row, "achieved_gbs": gbs, "frac": gbs / peak,
+                   "peak_kind": f"hbm_gbs of {peak_kind}"}
+    return out
+
+
 def amg_coarse_bytes(H, n: int) -> float:
     """Bytes per fine row that one V-cycle moves on levels >= 1: per level, down
     and up read each stored entry (int32 column + FP32 value) once, plus about
@@ -230,10 +271,114 @@ def run_reference(args):
 # ------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------
+def run_batched(args):
+    """256 uneven clouds (2k-262k points, sphere / ellipsoid / torus, K 12 or 20, 4 RHS) as one batch:
+    kNN per cloud on a stream pool, one batched assembly, one multigrid set-up per cloud, one persistent
+    solver launch for all; points/s over the whole batch, against the same clouds solved one at a time
+    by the plain FP64 path (row scaling)."""
+    import torch
+    from paper_1603_04100_gb300 import api, build
+    from paper_1603_04100_gb300 import inputs as I
+    from paper_1603_04100_gb300.batch import BatchPipeline
+    from paper_1603_04100_gb300.pipeline import Pipeline
+    build.build()
+    dev = torch.device("cuda", 0)
+    specs = I.batched_specs(256, seed=2)
+    probs = [sp.build() for sp in specs]
+    pts = [torch.from_numpy(p.pts).to(dev) for p in probs]
+    fs = [torch.from_numpy(np.ascontiguousarray(p.f)).to(dev) for p in probs]
+    sizes = [(p.pts.shape[0], p.k, p.f.shape[1]) for p in probs]
+    total = sum(s[0] for s in sizes)
+    out = {"metric": "MVGD points/s, 256-cloud batch (assembly+solve to 1e-8 rel)", "unit": "points/s",
+           "n_gpus": 1, "data": "synthetic", "config": {"workload": "batched: 256 clouds, N log-uniform 2,000-262,144 "
+           "(seed 2), sphere/ellipsoid/torus, K in {12, 20}, 4 RHS (x, yz, x^2-y^2, sin x e^y)", "points": total,
+           "rhs": sum(s[2] for s in sizes)}, "paths": {}}
+    for name, prec, precond in (("fp32_refine+amg", api.FP32_REFINE, 2), ("fp64+amg", api.FP64, 2)):
+        bp = BatchPipeline(sizes, prec=prec, precond=precond, device=dev)
+        for _ in range(max(1, args.warmup)):
+            bp.run(pts, fs)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(1, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            bp.run(pts, fs)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        infos = bp.infos()
+        st = sorted({i[3] for inf in infos for i in inf})
+        worst = max(i[2] for inf in infos for i in inf)
+        iters = [i[0] for inf in infos for i in inf]
+        out["paths"][name] = {"value": total / (statistics.mean(ms) * 1e-3), "ms": statistics.mean(ms),
+                              "statuses": st, "worst_relres": worst, "max_iters": max(iters),
+                              "mean_iters": statistics.mean(iters)}
+        del bp
+        torch.cuda.empty_cache()
+    # plain: the same clouds one at a time, FP64 with row scaling
+    t_plain = 0.0
+    for p, pt, f in zip(probs, pts, fs):
+        pipe = Pipeline(p.pts.shape[0], p.k, p.f.shape[1], prec=api.FP64, device=dev, precond=1, rtol=RTOL)
+        pipe.run(pt, f)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pipe.run(pt, f)
+        e1.record()
+        torch.cuda.synchronize()
+        t_plain += e0.elapsed_time(e1)
+        del pipe
+    out["paths"]["plain_fp64_one_by_one"] = {"value": total / (t_plain * 1e-3), "ms": t_plain}
+    best = max((k for k in out["paths"] if k != "plain_fp64_one_by_one"), key=lambda k: out["paths"][k]["value"])
+    out["value"] = out["paths"][best]["value"]
+    out["path"] = best
+    out["vs_plain"] = out["value"] / out["paths"]["plain_fp64_one_by_one"]["value"]
+    print(json.dumps(out))
+
+
+def run_served(args):
+    """The first --requests requests of the Poisson trace (200/s, 1k-1M points, 1-8 RHS) through the
+    serving loop (HBM-budget admission, continuous batching in epochs of the persistent solver)."""
+    import torch
+    from paper_1603_04100_gb300 import api, build
+    from paper_1603_04100_gb300 import inputs as I
+    from paper_1603_04100_gb300.serve import Server, requests_from_trace
+    build.build()
+    trace = I.serving_trace(count=args.requests, seed=3, rate_per_s=args.rate)
+    out = {"metric": "MVGD served points/s and latency (assembly+solve to 1e-8 rel)", "unit": "points/s",
+           "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": f"served: first {args.requests} requests of the Poisson trace (seed 3) at "
+                                  f"{args.rate:g}/s, N log-uniform 1,000-1,048,576, K 20, 1-8 RHS, 120 GB budget"},
+           "paths": {}}
+    for name, prec, precond in (("fp32_refine+amg", api.FP32_REFINE, 2), ("fp64+amg", api.FP64, 2)):
+        reqs = requests_from_trace(trace)
+        srv = Server("cuda:0", prec=prec, precond=precond, hbm_budget=120e9)
+        warm = requests_from_trace(trace[:2])
+        for r in warm:
+            r.arrival_s = 0.0
+        srv.serve(warm, realtime=False)
+        srv = Server("cuda:0", prec=prec, precond=precond, hbm_budget=120e9)
+        stats = srv.serve(reqs, realtime=True)
+        out["paths"][name] = stats
+        torch.cuda.empty_cache()
+    best = max(out["paths"], key=lambda k: out["paths"][k]["points_per_s"])
+    out["value"] = out["paths"][best]["points_per_s"]
+    out["p50_ms"] = out["paths"][best]["p50_ms"]
+    out["p99_ms"] = out["paths"][best]["p99_ms"]
+    out["path"] = best
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
     import torch
     import torch.distributed as dist
@@ -379,6 +524,10 @@ def main():
                     ((a - b) ** 2).sum() ** 0.5 / max((b ** 2).sum() ** 0.5, 1e-300))
         line["speedup_vs_plain_fp64_rowscale"] = {nm: results["fp64"]["ms"] / results[nm]["ms"] for nm in results}
     mixed = R["pipe"]
+
+    # a6 on its own: the standalone operator application on the assembled 1M operators
+    # (FP32 difference form on hi weights, FP64 standard form), L2 flushed before each launch
+    line["spmv"] = spmv_roofline(results, n, k, flush, stream, peak, peak_kind)
 
     if not args.no_e2e:
         pts_h = torch.from_numpy(pr.pts).pin_memory()

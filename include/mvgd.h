@@ -246,7 +246,8 @@ mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const doub
  *   - next level = Galerkin product P^T A P, P piecewise constant (FP64 sums,
  *     kept as FP32 for the cycle);
  *   - the first level with <= MVGD_AMG_COARSEST rows is inverted
- *     (Gauss-Jordan with partial pivoting, FP32);
+ *     (Gauss-Jordan with partial pivoting in FP32, then two Newton-Schulz
+ *     steps in FP64) and solved by an FP64 product with that inverse;
  *   - one V(1,1)-cycle with l1-Jacobi smoothing, d_i = 1 / sum_j |a_ij|, in FP32.
  * mvgd_amg_workspace_bytes: bytes of the hierarchy of an n-row operator with
  *   K neighbours (0 if n or K is out of range).
@@ -276,7 +277,8 @@ typedef struct {
     const double *val64;   /* levels >= 1: FP64 Galerkin sums */
     const int32_t *cnt;    /* levels >= 1: entries of each row (sorted by column) */
     const float *dinv;     /* [n] l1-Jacobi scaling */
-    const float *cinv;     /* coarsest level only: [n][n] row-major inverse */
+    const float *cinv;     /* coarsest level only: [n][n] FP32 Gauss-Jordan inverse, column-major (element (r, c) at c*n + r) */
+    const double *cinv64;  /* coarsest level only: [n][n] refined FP64 inverse, row-major (used by the cycle) */
 } mvgd_amg_info;
 
 size_t mvgd_amg_workspace_bytes(int64_t n, int32_t k);

@@ -66,7 +66,7 @@ def requests(items) -> C.Array:
 class AmgInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("stride", C.c_int32), ("status", C.c_int32),
                 ("width_max", C.c_int32), ("col", _P), ("val", _P), ("val64", _P), ("cnt", _P), ("dinv", _P),
-                ("cinv", _P)]
+                ("cinv", _P), ("cinv64", _P)]
 
 
 class AssembleItem(C.Structure):

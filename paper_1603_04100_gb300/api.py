@@ -250,10 +250,14 @@ class Hierarchy:
         v32 = sell_to_rows(grab(i.val, npad * w, torch.float32), n, w)
         return cnt, col, v64, v32, dinv
 
-    def coarsest_inverse(self) -> np.ndarray:
+    def coarsest_inverse(self, fp64: bool = True) -> np.ndarray:
+        """The coarsest level's inverse: the refined FP64 one the cycle uses, or the FP32 Gauss-Jordan one."""
         i = self.info(self.levels - 1)
         n = int(i.n)
-        return _device_view(i.cinv, n * n, torch.float32, self.ws.device).cpu().numpy().reshape(n, n)
+        if fp64:
+            return _device_view(i.cinv64, n * n, torch.float64, self.ws.device).cpu().numpy().reshape(n, n)
+        # stored column-major
+        return _device_view(i.cinv, n * n, torch.float32, self.ws.device).cpu().numpy().reshape(n, n).T.copy()
 
     def apply(self, b: torch.Tensor, stream=None) -> torch.Tensor:
         """x = one V-cycle applied to b (FP64 [n] or [n][nrhs], stored order)."""

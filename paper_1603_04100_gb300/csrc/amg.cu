@@ -10,7 +10,8 @@
 //     the rows of aggregate I and the columns of aggregate J), computed in
 //     FP64 one warp per coarse row, with a fixed summation order;
 //   * the first level with at most kAmgCoarsest rows is inverted by
-//     Gauss-Jordan elimination with partial pivoting (FP32, one block);
+//     Gauss-Jordan elimination with partial pivoting (FP32, one block),
+//     refined by two Newton-Schulz steps in FP64;
 //   * smoothing is l1-Jacobi (Baker, Falgout, Kolev, Yang 2011): d_i =
 //     1 / sum_j |a_ij|, positive on every row whatever the sign pattern.
 // Everything the V-cycle reads is FP32; the FP64 Galerkin values stay
@@ -59,6 +60,10 @@ AmgLayout amg_layout(void* ws, int64_t n, int k) {
     A.h.dense = cv.take<float>(nc * nc);
     A.h.cinv = cv.take<float>(nc * nc);
     A.h.piv = cv.take<int32_t>(nc);
+    A.h.dense64 = cv.take<double>(nc * nc);
+    A.h.cinv64 = cv.take<double>(nc * nc);
+    A.h.ns_x = cv.take<double>(nc * nc);
+    A.h.ns_t = cv.take<double>(nc * nc);
     A.h.bytes = cv.used;
     return A;
 }
@@ -197,26 +202,73 @@ __global__ void k_amg_slice_width(const AmgHeader* __restrict__ Hp, int l) {
     }
 }
 
-// The coarsest level as a dense FP32 matrix (zeroed first).
+// The coarsest level as dense FP32 and FP64 matrices (both zeroed first).
 __global__ void k_amg_dense(const AmgHeader* __restrict__ Hp, OpView O) {
     const AmgHeader& H = *Hp;
     const int m = H.nlev - 1;
     const int64_t nc = H.nc;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nc; r += (int64_t)gridDim.x * blockDim.x) {
         float* row = H.dense + r * nc;
+        double* row64 = H.dense64 + r * nc;
         if (m == 0) {
             const int k = H.k;
             const int64_t vb = (r / kSlice) * (int64_t)(kSlice * (k + 1)) + (r % kSlice);
-            row[r] = (float)(H.sigma - op_weight(O, vb));
+            row64[r] = H.sigma - op_weight(O, vb);
+            row[r] = (float)row64[r];
             for (int s = 0; s < k; s++) {
                 const int64_t j = O.col[(r / kSlice) * (int64_t)(kSlice * k) + (int64_t)s * kSlice + (r % kSlice)];
-                row[j] = (float)(-op_weight(O, vb + (int64_t)(s + 1) * kSlice));
+                row64[j] = -op_weight(O, vb + (int64_t)(s + 1) * kSlice);
+                row[j] = (float)row64[j];
             }
         } else {
             const AmgLevel& L = H.lv[m];
             const int64_t b = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
-            for (int s = 0; s < L.cnt[r]; s++) row[L.col[b + (int64_t)s * kSlice]] = L.val[b + (int64_t)s * kSlice];
+            for (int s = 0; s < L.cnt[r]; s++) {
+                const int64_t e = b + (int64_t)s * kSlice;
+                row64[L.col[e]] = L.val64[e];
+                row[L.col[e]] = L.val[e];
+            }
         }
+    }
+}
+
+// cinv64 = the FP32 inverse (column-major) in FP64, row-major.
+__global__ void k_amg_promote(const AmgHeader* __restrict__ Hp) {
+    const int64_t n = Hp->nc;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x)
+        Hp->cinv64[e] = (double)Hp->cinv[(e % n) * n + e / n];
+}
+
+// C = diag I + scale (A B) for small n x n row-major FP64 matrices: one block
+// per 32 x 32 tile of C, 32-wide k tiles staged in shared memory.  A Newton-
+// Schulz step X <- X (2I - A X) is two of these.
+constexpr int kGemmTile = 32;
+__global__ void __launch_bounds__(256) k_amg_dgemm(int n, const double* __restrict__ A, const double* __restrict__ B,
+                                                   double* __restrict__ Cm, double diag, double scale) {
+    __shared__ double As[kGemmTile][kGemmTile + 1], Bs[kGemmTile][kGemmTile + 1];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads, 4 rows each
+    const int row0 = blockIdx.y * kGemmTile, col = blockIdx.x * kGemmTile + tx;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k0 = 0; k0 < n; k0 += kGemmTile) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int r = ty + 8 * u;
+            As[r][tx] = (row0 + r < n && k0 + tx < n) ? A[(int64_t)(row0 + r) * n + k0 + tx] : 0.0;
+            Bs[r][tx] = (k0 + r < n && col < n) ? B[(int64_t)(k0 + r) * n + col] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < kGemmTile; kk++) {
+            const double b = Bs[kk][tx];
+#pragma unroll
+            for (int u = 0; u < 4; u++) acc[u] = fma(As[ty + 8 * u][kk], b, acc[u]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+        const int r = row0 + ty + 8 * u;
+        if (r < n && col < n) Cm[(int64_t)r * n + col] = scale * acc[u] + (r == col ? diag : 0.0);
     }
 }
 
@@ -225,25 +277,27 @@ __global__ void k_amg_dense(const AmgHeader* __restrict__ Hp, OpView O) {
 // and replaces a by the matrix of the eliminated system; the column swaps
 // are undone in reverse order at the end (the classical in-place form).
 constexpr int kInvThreads = 1024;
+constexpr int kInvWarps = kInvThreads / 32;
 __global__ void __launch_bounds__(kInvThreads) k_amg_invert(AmgHeader* Hp) {
-    const int64_t n = Hp->nc;
+    const int n = (int)Hp->nc;
     float* a = Hp->dense;
     int32_t* piv = Hp->piv;
     __shared__ float colk[kAmgCoarsest];
     __shared__ float rowk[kAmgCoarsest];
-    __shared__ float bv[kInvThreads / 32];
-    __shared__ int bi[kInvThreads / 32];
+    __shared__ int col_of[kAmgCoarsest];
+    __shared__ float bv[kInvWarps];
+    __shared__ int bi[kInvWarps];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) bad = 0;
     __syncthreads();
-    for (int64_t k = 0; k < n; k++) {
+    for (int k = 0; k < n; k++) {
         // pivot search
         float best = -1.0f;
         int bidx = INT_MAX;
-        for (int64_t i = k + tid; i < n; i += kInvThreads) {
+        for (int i = k + tid; i < n; i += kInvThreads) {
             const float v = fabsf(a[i * n + k]);
-            if (v > best) { best = v; bidx = (int)i; }
+            if (v > best) { best = v; bidx = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -256,35 +310,36 @@ __global__ void __launch_bounds__(kInvThreads) k_amg_invert(AmgHeader* Hp) {
         if (tid == 0) {
             float b = -1.0f;
             int p = INT_MAX;
-            for (int w = 0; w < kInvThreads / 32; w++)
+            for (int w = 0; w < kInvWarps; w++)
                 if (bv[w] > b || (bv[w] == b && bi[w] < p)) { b = bv[w]; p = bi[w]; }
             if (!(b > 0.0f) || !isfinite(b)) bad = 1;
-            piv[k] = p == INT_MAX ? (int)k : p;
+            piv[k] = p == INT_MAX ? k : p;
         }
         __syncthreads();
         if (bad) break;
-        const int64_t p = piv[k];
+        const int p = piv[k];
         if (p != k)
-            for (int64_t j = tid; j < n; j += kInvThreads) {
+            for (int j = tid; j < n; j += kInvThreads) {
                 const float t = a[k * n + j];
                 a[k * n + j] = a[p * n + j];
                 a[p * n + j] = t;
             }
         __syncthreads();
         const float inv = 1.0f / a[k * n + k];
-        for (int64_t i = tid; i < n; i += kInvThreads) {
+        for (int i = tid; i < n; i += kInvThreads) {
             colk[i] = a[i * n + k];
             rowk[i] = (i == k) ? inv : a[k * n + i] * inv;
         }
         __syncthreads();
-        for (int64_t e = tid; e < n * n; e += kInvThreads) {
-            const int64_t i = e / n, j = e % n;
+        // a warp per row, lanes along the row (coalesced); no index division
+        for (int i = wid; i < n; i += kInvWarps) {
+            float* row = a + i * n;
             if (i == k) {
-                a[e] = rowk[j];
-            } else if (j == k) {
-                a[e] = -colk[i] * inv;
+                for (int j = lane; j < n; j += 32) row[j] = rowk[j];
             } else {
-                a[e] = fmaf(-colk[i], rowk[j], a[e]);
+                const float cik = colk[i];
+#pragma unroll 4
+                for (int j = lane; j < n; j += 32) row[j] = (j == k) ? -cik * inv : fmaf(-cik, rowk[j], row[j]);
             }
         }
         __syncthreads();
@@ -293,18 +348,19 @@ __global__ void __launch_bounds__(kInvThreads) k_amg_invert(AmgHeader* Hp) {
         if (tid == 0) atomicCAS((int*)&Hp->status, 0, (int)MVGD_EDEGENERATE);
         return;
     }
-    // undo the column interchanges, last first
-    for (int64_t k = n - 1; k >= 0; k--) {
-        const int64_t p = piv[k];
-        if (p != k)
-            for (int64_t i = tid; i < n; i += kInvThreads) {
-                const float t = a[i * n + k];
-                a[i * n + k] = a[i * n + p];
-                a[i * n + p] = t;
-            }
-        __syncthreads();
+    // undo the column interchanges (last first) as one permutation, stored transposed:
+    // result column c is column col_of[c] of the eliminated matrix
+    if (tid == 0) {
+        for (int c = 0; c < n; c++) col_of[c] = c;
+        for (int k = n - 1; k >= 0; k--) {
+            const int p = piv[k], t = col_of[k];
+            col_of[k] = col_of[p];
+            col_of[p] = t;
+        }
     }
-    for (int64_t e = tid; e < n * n; e += kInvThreads) Hp->cinv[e] = a[e];
+    __syncthreads();
+    for (int c = wid; c < n; c += kInvWarps)
+        for (int r = lane; r < n; r += 32) Hp->cinv[c * n + r] = a[r * n + col_of[c]];  // column-major
 }
 
 int grid_for(int64_t threads) {
@@ -423,6 +479,9 @@ MVGD_API mvgd_status mvgd_amg_setup(const mvgd_ell* L, double sigma, void* amg_w
     if (amg_bytes < A.h.bytes) return MVGD_EWORKSPACE;
     A.h.sigma = sigma;
     A.h.col0 = L->col;
+    A.h.val0 = L->val;
+    A.h.val0_lo = L->val_lo;
+    A.h.prec0 = L->prec;
     A.h.status = MVGD_OK;
     A.h.width_max = 0;
     cudaStream_t s = (cudaStream_t)stream;
@@ -434,9 +493,25 @@ MVGD_API mvgd_status mvgd_amg_setup(const mvgd_ell* L, double sigma, void* amg_w
         k_amg_coarsen<<<grid_for(nc * kWarp), 256, 0, s>>>(A.hdr, O, l);
         k_amg_slice_width<<<grid_for(nc / kSlice + 1), 256, 0, s>>>(A.hdr, l + 1);
     }
-    MVGD_CUDA_TRY(cudaMemsetAsync(A.h.dense, 0, sizeof(float) * A.h.nc * A.h.nc, s));
-    k_amg_dense<<<grid_for(A.h.nc), 256, 0, s>>>(A.hdr, O);
+    const int64_t nc = A.h.nc;
+    MVGD_CUDA_TRY(cudaMemsetAsync(A.h.dense, 0, sizeof(float) * nc * nc, s));
+    MVGD_CUDA_TRY(cudaMemsetAsync(A.h.dense64, 0, sizeof(double) * nc * nc, s));
+    k_amg_dense<<<grid_for(nc), 256, 0, s>>>(A.hdr, O);
     k_amg_invert<<<1, kInvThreads, 0, s>>>(A.hdr);
+    // two Newton-Schulz steps X <- X (2I - A X) in FP64 from the FP32 inverse: its
+    // residual (~1e-5) squares each step, to the FP64 level
+    k_amg_promote<<<grid_for(nc * nc), 256, 0, s>>>(A.hdr);
+    const dim3 gg((unsigned)((nc + kGemmTile - 1) / kGemmTile), (unsigned)((nc + kGemmTile - 1) / kGemmTile));
+    double* X = A.h.cinv64;
+    double* Xn = A.h.ns_x;
+    for (int step = 0; step < 2; step++) {
+        k_amg_dgemm<<<gg, 256, 0, s>>>((int)nc, A.h.dense64, X, A.h.ns_t, 2.0, -1.0);  // T = 2I - A X
+        k_amg_dgemm<<<gg, 256, 0, s>>>((int)nc, X, A.h.ns_t, Xn, 0.0, 1.0);          // X' = X T
+        double* t = X;
+        X = Xn;
+        Xn = t;
+    }
+    // after an even number of steps the result is back in cinv64
     return launch_status();
 }
 
@@ -458,6 +533,7 @@ MVGD_API mvgd_status mvgd_amg_describe(const void* amg_ws, int32_t level, mvgd_a
     out->cnt = L.cnt;
     out->dinv = L.dinv;
     out->cinv = level == h.nlev - 1 ? h.cinv : nullptr;
+    out->cinv64 = level == h.nlev - 1 ? h.cinv64 : nullptr;
     return MVGD_OK;
 }
 

@@ -36,8 +36,15 @@ struct AmgHeader {
     double sigma;
     const int32_t* col0;  // the operator's columns (level 0)
     AmgLevel lv[kAmgMaxLevels];
+    const void* val0;   // the operator's weights (FP64, or FP32 hi) and
+    const float* val0_lo;  //   lo (mixed format), for an exact coarsest residual on one-level hierarchies
+    int32_t prec0, pad0;
     float* dense;       // [nc][nc] the coarsest level as a dense matrix (FP32, set-up scratch)
-    float* cinv;        // [nc][nc] its inverse, row-major
+    float* cinv;        // [nc][nc] its FP32 Gauss-Jordan inverse, column-major: cinv[c * nc + r] = (A_c^-1)[r][c]
+    double* dense64;    // [nc][nc] the coarsest level, FP64 row-major
+    double* cinv64;     // [nc][nc] the inverse after two Newton-Schulz steps in FP64, row-major (what the cycle uses)
+    double* ns_x;       // [nc][nc] set-up scratch
+    double* ns_t;       // [nc][nc] set-up scratch
     int32_t* piv;       // [nc] set-up scratch
     int64_t nc;         // rows of the coarsest level
     size_t bytes;       // whole hierarchy

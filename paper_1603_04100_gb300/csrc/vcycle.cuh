@@ -107,14 +107,18 @@ __device__ __forceinline__ float vup_row(const AmgHeader& H, int l, int64_t r, i
     return yi + xc + H.lv[l].dinv[r] * (ri - apx);
 }
 
-// Coarsest solve, one warp per row rho: x[rho] = sum_c Cinv[rho][c] b[c].
+// Coarsest solve, one warp per row rho: x[rho] = sum_c X[rho][c] b[c] with X
+// the FP64 inverse (row-major, lanes along the row) and the sum in FP64.  An
+// FP32 product with the inverse carries cond(A_c) ~ 1e4 times the FP32
+// rounding (about 1e-3 relative at 1M points), which cost the outer Krylov
+// solve ~20 % more iterations; in FP64 the cost is ~8 FP64 FMAs per lane.
 template <typename BOF>
 __device__ __forceinline__ float coarse_row(const AmgHeader& H, int64_t rho, BOF&& b_of) {
     const int64_t nc = H.nc;
-    const float* row = H.cinv + rho * nc;
-    float acc = 0.0f;
-    for (int64_t c = lane_id(); c < nc; c += kWarp) acc = fmaf(row[c], b_of(c), acc);
-    return warp_sum(acc);
+    const double* row = H.cinv64 + rho * nc;
+    double acc = 0.0;
+    for (int64_t c = lane_id(); c < nc; c += kWarp) acc = fma(row[c], (double)b_of(c), acc);
+    return (float)warp_sum(acc);
 }
 
 }  // namespace mvgd

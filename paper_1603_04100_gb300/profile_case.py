@@ -2,6 +2,7 @@
 random unit sphere (K = 20), run twice, for Nsight Compute captures.
 
     python -m paper_1603_04100_gb300.profile_case [n] [prec: 0 FP64 | 1 FP32+refine] [iterations]
+                                                  [precond: 1 row scaling | 2 multigrid]
 """
 import sys
 
@@ -15,6 +16,7 @@ def main(argv):
     n = int(argv[1]) if len(argv) > 1 else 262144
     prec = int(argv[2]) if len(argv) > 2 else 1
     iters = int(argv[3]) if len(argv) > 3 else 30
+    precond = int(argv[4]) if len(argv) > 4 else 1
     dev = torch.device("cuda:0")
     pr = I.random_sphere_problem(n, 20, seed=0)
     pts = torch.from_numpy(pr.pts).to(dev)
@@ -24,7 +26,7 @@ def main(argv):
         op = api.assemble(pts, nbr, prec=prec, order=order)
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0.record()
-        r = api.solve(op, f, rtol=1e-8, precond=1, maxit=iters)
+        r = api.solve(op, f, rtol=1e-8, precond=precond, maxit=iters)
         t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)

@@ -216,10 +216,10 @@ class Server:
                 waiting.append(pending.popleft())
             admit = []
             while (waiting and len(active) + len(admit) < self.max_active
-                   and self.used + request_bytes(waiting[0].n, waiting[0].k, waiting[0].nrhs, self.prec)
+                   and self.used + request_bytes(waiting[0].n, waiting[0].k, waiting[0].nrhs, self.prec, self.precond)
                    <= self.budget):
                 r = waiting.popleft()
-                self.used += request_bytes(r.n, r.k, r.nrhs, self.prec)
+                self.used += request_bytes(r.n, r.k, r.nrhs, self.prec, self.precond)
                 r.admitted_s = now
                 admit.append(r)
             if not admit and waiting and not active:

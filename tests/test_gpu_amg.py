@@ -73,15 +73,19 @@ def test_coarsest_inverse(n):
     from paper_1603_04100_gb300 import api
     _, nbr, val = _oracle_operator(n, 20, 32)
     H = api.amg_setup(api.operator_from_rows(nbr, val, api.FP64, dev), 1.0)
-    X = H.coarsest_inverse().astype(np.float64)
     Ac = OA.hierarchy(val, nbr, 1.0)[-1].dense()
     nc = Ac.shape[0]
     want = np.linalg.inv(Ac)
     cond = np.linalg.cond(Ac)
-    # FP32 Gauss-Jordan with partial pivoting: residual and forward error of order n u cond
-    u32 = 2.0 ** -24
-    assert np.abs(Ac @ X - np.eye(nc)).max() <= 4 * nc * u32 * cond
-    assert np.linalg.norm(X - want) / np.linalg.norm(want) <= 4 * nc * u32 * cond
+    # FP32 Gauss-Jordan with partial pivoting: residual and forward error of order n u32 cond
+    X32 = H.coarsest_inverse(fp64=False).astype(np.float64)
+    u32, u64 = 2.0 ** -24, 2.0 ** -53
+    assert np.abs(Ac @ X32 - np.eye(nc)).max() <= 4 * nc * u32 * cond
+    assert np.linalg.norm(X32 - want) / np.linalg.norm(want) <= 4 * nc * u32 * cond
+    # two Newton-Schulz steps in FP64 square that residual twice: down to the FP64 level
+    X = H.coarsest_inverse()
+    assert np.abs(Ac @ X - np.eye(nc)).max() <= 4 * nc * u64 * cond
+    assert np.linalg.norm(X - want) / np.linalg.norm(want) <= 4 * nc * u64 * cond
 
 
 @pytest.mark.parametrize("n,nrhs", [(20000, 1), (9000, 3), (300, 2)])
