@@ -248,7 +248,11 @@ mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const doub
  *   - the first level with <= MVGD_AMG_COARSEST rows is inverted
  *     (Gauss-Jordan with partial pivoting in FP32, then two Newton-Schulz
  *     steps in FP64) and solved by an FP64 product with that inverse;
- *   - one V(1,1)-cycle with l1-Jacobi smoothing, d_i = 1 / sum_j |a_ij|, in FP32.
+ *   - one V(1,1)-cycle in FP32 with Jacobi smoothing x += d (b - A x):
+ *     d_i = MVGD_AMG_JACOBI_OMEGA / a_ii on rows with a strong diagonal
+ *     (a_ii > MVGD_AMG_JACOBI_THETA sum_j |a_ij|), the l1 scaling
+ *     d_i = 1 / sum_j |a_ij| on the others (MVGD rows with few neighbours on
+ *     irregular samples can have a small or negative diagonal).
  * mvgd_amg_workspace_bytes: bytes of the hierarchy of an n-row operator with
  *   K neighbours (0 if n or K is out of range).
  * mvgd_amg_setup: builds the hierarchy of sigma I - L in amg_ws (DEVICE,
@@ -265,6 +269,8 @@ mvgd_status mvgd_solve(const mvgd_ell *L, int32_t nrhs, double sigma, const doub
 #define MVGD_AMG_AGG 8
 #define MVGD_AMG_COARSEST 512
 #define MVGD_AMG_MAX_WIDTH 64
+#define MVGD_AMG_JACOBI_OMEGA 0.9
+#define MVGD_AMG_JACOBI_THETA 0.3
 
 typedef struct {
     int64_t n;             /* rows of this level */
@@ -276,7 +282,7 @@ typedef struct {
     const float *val;      /* FP32 values (level 0: the operator's weights, slot 0 = self) */
     const double *val64;   /* levels >= 1: FP64 Galerkin sums */
     const int32_t *cnt;    /* levels >= 1: entries of each row (sorted by column) */
-    const float *dinv;     /* [n] l1-Jacobi scaling */
+    const float *dinv;     /* [n] the smoother's scaling d_i (FP64 choice, rounded once) */
     const float *cinv;     /* coarsest level only: [n][n] FP32 Gauss-Jordan inverse, column-major (element (r, c) at c*n + r) */
     const double *cinv64;  /* coarsest level only: [n][n] refined FP64 inverse, row-major (used by the cycle) */
 } mvgd_amg_info;

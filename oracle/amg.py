@@ -18,7 +18,11 @@ Definitions (Braess 1995 for plain aggregation; Baker, Falgout, Kolev and Yang
   aggregate I and columns j of aggregate J;
 * coarsening stops at the first level with at most `coarsest` rows, which is
   solved exactly (its dense inverse);
-* the smoother is one l1-Jacobi step x += D^-1 (b - A x), D_ii = sum_j |a_ij|;
+* the smoother is one Jacobi step x += D^-1 (b - A x) with a per-row choice
+  of D: d_i = OMEGA / a_ii on rows whose diagonal is strong (a_ii > THETA
+  sum_j |a_ij|), and the l1 scaling d_i = 1 / sum_j |a_ij| elsewhere (rows with
+  a small or non-positive diagonal, which MVGD rows with few neighbours on
+  irregular samples do have);
 * one V-cycle on b: y = D^-1 b (pre-smoothing from zero), r = b - A y,
   x_c = V-cycle of the next level on P^T r, x = y + P x_c, then one
   post-smoothing step x += D^-1 (b - A x).
@@ -29,11 +33,14 @@ import numpy as np
 
 AGG = 8
 COARSEST = 512
+OMEGA = 0.9   # damping of the Jacobi step on diagonally strong rows
+THETA = 0.3   # a row is diagonally strong when a_ii > THETA * sum_j |a_ij|
 
 
 class Level:
     """One level: a sparse matrix as (rows, cols, vals) sorted by (row, col),
-    without duplicate entries, plus its l1 diagonal."""
+    without duplicate entries, plus its diagonal, its row l1 norms and the
+    smoother's scaling d."""
 
     def __init__(self, n: int, rows, cols, vals):
         self.n = int(n)
@@ -46,6 +53,11 @@ class Level:
         self.vals = summed
         self.l1 = np.zeros(self.n)
         np.add.at(self.l1, self.rows, np.abs(self.vals))
+        self.diag = np.zeros(self.n)
+        on = self.rows == self.cols
+        self.diag[self.rows[on]] = self.vals[on]
+        strong = self.diag > THETA * self.l1
+        self.d = np.where(strong, OMEGA / np.where(strong, self.diag, 1.0), 1.0 / self.l1)
 
     def matvec(self, x: np.ndarray) -> np.ndarray:
         y = np.zeros(self.n)
@@ -97,7 +109,7 @@ def vcycle(levels, b: np.ndarray, agg: int = AGG, inv: np.ndarray | None = None,
     if lvl == len(levels) - 1:
         X = coarsest_inverse(levels) if inv is None else inv
         return X @ b
-    d = 1.0 / A.l1
+    d = A.d
     y = d * b
     r = b - A.matvec(y)
     bc = np.zeros(levels[lvl + 1].n)

@@ -11,6 +11,13 @@ constexpr int kAmgCoarsest = MVGD_AMG_COARSEST;  // a level this small is solved
 constexpr int kAmgStride = MVGD_AMG_MAX_WIDTH;   // slots per coarse row in the sliced layout
 constexpr int kAmgMaxLevels = 12;
 
+// The smoother's scaling of a row with diagonal a_ii and l1 norm sum_j |a_ij|
+// (FP64, rounded once): omega / a_ii on a strong diagonal, else the l1 scaling.
+__host__ __device__ inline float amg_smoother_scale(double diag, double l1) {
+    if (diag > MVGD_AMG_JACOBI_THETA * l1) return (float)(MVGD_AMG_JACOBI_OMEGA / diag);
+    return l1 > 0.0 ? (float)(1.0 / l1) : 1.0f;
+}
+
 // One level.  Level 0 is the operator itself: its neighbour columns (the
 // operator's `col`, K slots) and an FP32 copy of its weights ([n_pad][K+1],
 // slot 0 = the point itself), so that A x = sigma x_i - (w_0 x_i + sum_s w_s x_j).
@@ -23,7 +30,7 @@ struct AmgLevel {
     double* val64;   // level >= 1: FP64 values (the Galerkin sums before rounding)
     int32_t* cnt;    // level >= 1: [n] entries per row
     int32_t* sw;     // level >= 1: [n_pad / 32] widest row of each slice
-    float* dinv;     // [n] 1 / sum_j |a_ij|  (l1-Jacobi)
+    float* dinv;     // [n] the smoother's scaling (amg_smoother_scale)
     float* rs;       // level >= 1: [n] row sums sum_j a_ij (FP64 sums, rounded once)
 };
 
@@ -49,6 +56,20 @@ struct AmgHeader {
     int64_t nc;         // rows of the coarsest level
     size_t bytes;       // whole hierarchy
 };
+
+// Lanes that share one row of level l >= 1 in a V-cycle step, a function of the
+// level's size alone (so a request's arithmetic does not depend on what else
+// shares the launch).  A coarse row holds 10-60 entries; one lane per row makes
+// each step a chain of that many dependent L2 round trips on a level too small
+// to fill the GPU, so a level takes the largest G (a power of two, <= 32) that
+// keeps rows x G within one pass of 152 SMs x 3 blocks x 256 threads.  A block
+// of 256 threads takes 256 / G rows: always whole aggregates.
+constexpr int64_t kAmgLanesOnePass = 152 * 3 * 256;
+__host__ __device__ inline int amg_group(int64_t rows) {
+    int g = 1;
+    while (g < 32 && rows * 2 * g <= kAmgLanesOnePass) g *= 2;
+    return g;
+}
 
 // Level sizes for a fine size n: n_0 = n, n_{l+1} = ceil(n_l / kAmgAgg) while
 // n_l > kAmgCoarsest.  Returns the level count (0 if it would exceed the maximum).

@@ -699,7 +699,7 @@ struct ChunkTable {
 struct ReqTable {
     const Prob* const* prob;       // [count]
     ChunkTable fine;               // kCh-row tiles of level 0 (every Krylov phase; V-cycle level 0)
-    ChunkTable lvl[kAmgMaxLevels]; // [l], 1 <= l < mlev: kCh-row tiles of multigrid level l
+    ChunkTable lvl[kAmgMaxLevels]; // [l], 1 <= l < mlev: kThreads / amg_group(n_l)-row units of level l
     ChunkTable coarse;             // 8-row groups (a warp each) of every coarsest level
     int mlev;                      // largest (levels - 1) among the requests
 };
@@ -784,6 +784,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     __shared__ double fin[kThreads / 32][kChan * QT];
     __shared__ double tot[kChan * QT];
     __shared__ int last;
+    __shared__ float vagg[kThreads / kAmgAgg];  // a block's row residuals on a small level (agg_sum)
     __shared__ __align__(8) uint64_t stage_bar[kThreads / 32][2];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // this warp's nbuf slice buffers: kmax column slots, then kmax + 1 weight slots each
@@ -810,8 +811,11 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     bool inner[QT], restart[QT];
     bool any_inner = false, any_restart = false, all_done = true;
     float c1[QT], c2[QT];
+    // the request whose state S holds, while no phase has advanced it since
+    int held = -1;
     // Loads request ri's per-RHS state into S (block-wide) and its masks.
     auto enter = [&](int ri, int ph) {
+        held = ri;
         __syncthreads();
         const Prob& P = *tab.prob[ri];
         // a K above the one the staging buffers were sized for (a wrong K in the
@@ -935,6 +939,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         // read only after it, so every block takes the same exit decision
         if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
             *ctl.stop = 1;
+        if (reduce) held = -1;  // the states were advanced at the arrivals
         const bool ok = grid_sync(ctl.bar, ctl.err, ctl.limit);
         trace_step(ctl, (unsigned)ph);
         return ok;
@@ -949,7 +954,9 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             const int ri = T.chunk_req[c];
             if (ri != cur) {
                 cur = ri;
-                enter(ri, P_PRE_A);
+                // V-cycle steps leave the states alone: the one loaded by the
+                // preceding PRE phase (or step) stays valid
+                if (ri != held) enter(ri, P_PRE_A);
             }
             const Prob& P = *tab.prob[ri];
             const int m = P.amg_levels - 1;  // the request's coarsest level
@@ -976,9 +983,14 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 continue;
             }
             const int64_t nl = H.lv[l].n;
-            const int64_t r = (int64_t)lc * kCh + tid;
-            if (r - lane >= nl) continue;  // whole warps past the level's end
+            // level 0: a lane per row (staged slices); level >= 1: G lanes per row
+            const int G = l == 0 ? 1 : amg_group(nl);
+            const int64_t r = (int64_t)lc * (kThreads / G) + tid / G;
             const bool valid = r < nl;
+            // whole warps past the level's end have nothing to do, except in a down
+            // step whose aggregates span warps (G >= 8: block barriers in agg_sum)
+            const bool warp_idle = (int64_t)lc * (kThreads / G) + (wid * kWarp) / G >= nl;
+            if (warp_idle && (kind == V_UP || G < 8)) continue;
             // level 0 reads the operator's slice from a staged buffer, like A and B
             const int* colS = nullptr;
             const float* w0S = nullptr;
@@ -1009,9 +1021,9 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 if (l == 0 && !st.wait(b, ctl.err)) continue;
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
-                    if (!inner[q]) continue;
-                    vdown_row(H, l, r, valid, Q, q, bi[q], yi[q], [&](int64_t j) { return Y[j * Q + q]; }, P.vr[l],
-                              P.vb[l + 1], Yn, a0);
+                    if (!inner[q]) continue;  // block-uniform
+                    vdown_row(H, l, G, r, valid, Q, q, bi[q], yi[q], [&](int64_t j) { return Y[j * Q + q]; },
+                              P.vr[l], P.vb[l + 1], Yn, a0, vagg);
                 }
             } else {
                 const float* Xc = P.vx[l + 1];
@@ -1022,13 +1034,14 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                     rr[q] = (valid && inner[q]) ? P.vr[l][r * Q + q] : 0.0f;
                 }
                 if (l == 0 && !st.wait(b, ctl.err)) continue;
-                if (!valid) continue;
+                if (!valid && G == 1) continue;
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
                     if (!inner[q]) continue;
                     const int64_t e = r * Q + q;
-                    const float x = vup_row(H, l, r, Q, q, yi[q], rr[q], [&](int64_t J) { return Xc[J * Q + q]; },
-                                            a0);
+                    const float x = vup_row(H, l, G, r, valid, yi[q], rr[q],
+                                            [&](int64_t J) { return Xc[J * Q + q]; }, a0);
+                    if (!valid || (lane & (G - 1)) != 0) continue;
                     if (l == 0) X0[e] = (VT)x;
                     else P.vx[l][e] = x;
                 }
@@ -1146,9 +1159,12 @@ CtlLayout ctl_layout(void* ws, int max_req, int64_t max_chunks) {
     C.words = cv.take<int>(4);
     C.prob = cv.take<const Prob*>(max_req);
     for (int t = 0; t <= kAmgMaxLevels; t++) {
-        // level l >= 1 has at most max_chunks / 8^l + max_req tiles; the bound below is looser
+        // level l >= 1 of a request has n_l <= n / 8^l + 1 rows in ceil(n_l G / kThreads)
+        // <= n_l / 8 + 1 units (G <= 32): over all requests at most
+        // total_rows / 8^(l+1) + 2 count (one more per request kept as margin), and
+        // total_rows <= kCh max_chunks
         const int64_t units = t == kAmgMaxLevels ? (int64_t)max_req * kCoarseUnits
-                                                  : (t == 0 ? max_chunks : max_chunks / kAmgAgg + max_req);
+                              : (t == 0 ? max_chunks : ((int64_t)kCh * max_chunks >> (3 * (t + 1))) + 3 * max_req);
         C.chunk_req[t] = cv.take<int>(units);
         C.chunk_base[t] = cv.take<int>(max_req);
     }
@@ -1504,7 +1520,12 @@ MVGD_API mvgd_status mvgd_iterate(const mvgd_request* reqs, int32_t count, int32
                 const int nl = amg ? amg_levels(R.n, sizes) : 1;
                 if (t == 0) A.nchunk[i] = (int)((R.n + kCh - 1) / kCh);
                 else if (coarse) A.nchunk[i] = (int)((sizes[nl - 1] + kThreads / kWarp - 1) / (kThreads / kWarp));
-                else A.nchunk[i] = t < nl - 1 ? (int)((sizes[t] + kCh - 1) / kCh) : 0;
+                else if (t < nl - 1) {
+                    const int64_t rows = kThreads / amg_group(sizes[t]);  // rows per unit
+                    A.nchunk[i] = (int)((sizes[t] + rows - 1) / rows);
+                } else {
+                    A.nchunk[i] = 0;
+                }
                 units += A.nchunk[i];
             }
             k_build_table<<<1, 256, 0, s>>>(A, g, t == 0 ? C.prob : nullptr, C.chunk_req[t], C.chunk_base[t], C.bar,

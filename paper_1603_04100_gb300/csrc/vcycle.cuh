@@ -18,14 +18,6 @@
 
 namespace mvgd {
 
-// Sum over the 8 lanes of each aggregate (lanes 8g .. 8g+7).
-__device__ __forceinline__ float agg_sum8(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    return v;
-}
-
 // Every product below is taken in difference form, sum_j a_ij (x_j - x_i) +
 // (sum_j a_ij) x_i, with the row sum exact: rows of L sum to zero, so level 0
 // is sigma x_i - sum_s w_s (x_j - x_i), and a Galerkin row sums to sigma times
@@ -61,50 +53,86 @@ __device__ __forceinline__ float a0_row_staged(const int* colS, const float* w, 
     return sigma * xi - acc;
 }
 
-// Level-l (>= 1) product with the explicit Galerkin matrix; padding slots are
-// (own row, 0), so every lane runs to the slice's widest row.
+// Level-l (>= 1) product with the explicit Galerkin matrix, row r taken by the
+// G lanes of its group (G a power of two <= 32, groups aligned in the warp):
+// lane `sub` sums slots sub, sub + G, ... and the group adds its partials by a
+// butterfly, so every lane of the group returns the same value.  Padding slots
+// are (own row, 0), so every lane runs to the slice's widest row.  Lanes of
+// invalid rows return 0 but take part in the shuffles.
 template <typename XV>
-__device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, float xi, XV&& xv) {
-    const int64_t base = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
-    const int w = Lv.sw[r / kSlice];
+__device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, bool valid, int G, float xi, XV&& xv) {
     float acc = 0.0f;
+    if (valid) {
+        const int64_t base = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
+        const int w = Lv.sw[r / kSlice];
 #pragma unroll 4
-    for (int s = 0; s < w; s++)
-        acc = fmaf(Lv.val[base + s * kSlice], xv((int64_t)Lv.col[base + s * kSlice]) - xi, acc);
-    return fmaf(Lv.rs[r], xi, acc);
+        for (int s = (int)(lane_id() & (G - 1)); s < w; s += G)
+            acc = fmaf(Lv.val[base + s * kSlice], xv((int64_t)Lv.col[base + s * kSlice]) - xi, acc);
+    }
+    for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return valid ? fmaf(Lv.rs[r], xi, acc) : 0.0f;
 }
 
-// Down step of level l for right-hand side q of the warp's rows.  `b` is the
-// row's own right-hand side (level 0: the Krylov vector, rounded to FP32),
-// `y_of(j)` the pre-smoothed y_l at any row j (already stored: level 0 by the
-// step that formed b_0, level >= 1 by the restriction that formed b_l).
-// Writes r_l, and b_{l+1}, y_{l+1} of the aggregate (its first lane).
-// `a0(xi, xv)` is the level-0 product (from global memory or a staged slice).
-template <typename YOF, typename A0>
-__device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int64_t r, bool valid, int Q, int q, float b,
-                                          float yi, YOF&& y_of, float* R, float* Bn, float* Yn, A0&& a0) {
-    float res = 0.0f;
-    if (valid) {
-        const float ay = (l == 0) ? a0(yi, y_of) : al_row(H.lv[l], r, yi, y_of);
-        res = b - ay;
-        R[r * Q + q] = res;
+// Sum of a value over the 8 rows of each aggregate, rows of G lanes each,
+// returned to the lanes of the aggregate's first row (((v0+v1)+(v2+v3))+
+// ((v4+v5)+(v6+v7)) for every G).  Up to G = 4 an aggregate lies in one warp
+// and the sum is a butterfly; above, it spans warps and goes through `agg`
+// (kThreads / G floats of shared memory) between two block barriers, so every
+// thread of the block must call it.
+__device__ __forceinline__ float agg_sum(float v, int G, float* agg) {
+    if (G <= 4) {
+        for (int o = G; o < kAmgAgg * G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
     }
-    const float bc = agg_sum8(res);  // rows past the end contribute 0
-    if (valid && (r % kAmgAgg) == 0) {
+    const int i = (int)threadIdx.x / G;  // the row's place in the block
+    if ((threadIdx.x & (G - 1)) == 0) agg[i] = v;
+    __syncthreads();
+    const float* a = agg + (i & ~(kAmgAgg - 1));
+    v = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+    __syncthreads();
+    return v;
+}
+
+// Down step of level l for right-hand side q of row r (G lanes a row; level 0
+// takes G = 1).  `b` is the row's own right-hand side (level 0: the Krylov
+// vector, rounded to FP32), `y_of(j)` the pre-smoothed y_l at any row j
+// (already stored: level 0 by the step that formed b_0, level >= 1 by the
+// restriction that formed b_l).  Writes r_l, and b_{l+1}, y_{l+1} of the
+// aggregate (the first lane of its first row).  `a0(xi, xv)` is the level-0
+// product (from global memory or a staged slice).  With G >= 8 every thread
+// of the block calls it (see agg_sum).
+template <typename YOF, typename A0>
+__device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int G, int64_t r, bool valid, int Q, int q,
+                                          float b, float yi, YOF&& y_of, float* R, float* Bn, float* Yn, A0&& a0,
+                                          float* agg) {
+    const bool lead = (lane_id() & (G - 1)) == 0;
+    float res = 0.0f;
+    if (l == 0) {
+        if (valid) res = b - a0(yi, y_of);
+    } else {
+        res = b - al_row(H.lv[l], r, valid, G, yi, y_of);
+    }
+    if (!valid) res = 0.0f;  // rows past the end contribute 0
+    if (valid && lead) R[r * Q + q] = res;
+    const float bc = agg_sum(res, G, agg);
+    if (valid && lead && (r % kAmgAgg) == 0) {
         const int64_t I = r / kAmgAgg;
         Bn[I * Q + q] = bc;
         if (Yn) Yn[I * Q + q] = H.lv[l + 1].dinv[I] * bc;
     }
 }
 
-// Up step of level l: x_l = y_l + P x_{l+1} + d_l (r_l - A_l P x_{l+1}).
+// Up step of level l: x_l = y_l + P x_{l+1} + d_l (r_l - A_l P x_{l+1}), for
+// row r of G lanes (level 0: G = 1); every lane of a valid row returns x.
 template <typename XC, typename A0>
-__device__ __forceinline__ float vup_row(const AmgHeader& H, int l, int64_t r, int Q, int q, float yi, float ri,
+__device__ __forceinline__ float vup_row(const AmgHeader& H, int l, int G, int64_t r, bool valid, float yi, float ri,
                                          XC&& xc_of, A0&& a0) {
-    const float xc = xc_of(r / kAmgAgg);
+    const float xc = valid ? xc_of(r / kAmgAgg) : 0.0f;
     auto pxc = [&](int64_t j) { return xc_of(j / kAmgAgg); };
-    const float apx = (l == 0) ? a0(xc, pxc) : al_row(H.lv[l], r, xc, pxc);
-    return yi + xc + H.lv[l].dinv[r] * (ri - apx);
+    float apx;
+    if (l == 0) apx = valid ? a0(xc, pxc) : 0.0f;
+    else apx = al_row(H.lv[l], r, valid, G, xc, pxc);
+    return valid ? yi + xc + H.lv[l].dinv[r] * (ri - apx) : 0.0f;
 }
 
 // Coarsest solve, one warp per row rho: x[rho] = sum_c X[rho][c] b[c] with X

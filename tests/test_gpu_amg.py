@@ -41,9 +41,10 @@ def test_hierarchy_matches_oracle(n, k, prec_name):
     i0 = H.info(0)
     assert i0.status == 0, i0.status
     assert H.levels == len(levels)
-    # level 0: the l1 scaling 1 / (|sigma - w_0| + sum |w_s|), rounded once to FP32
+    # level 0: the smoother's scaling (omega / a_ii on strong rows, else 1 / sum |a_ij|),
+    # from FP64 sums rounded once to FP32
     (d0,) = H.level_rows(0)
-    np.testing.assert_allclose(d0, 1.0 / levels[0].l1, rtol=2 ** -23, atol=0)
+    np.testing.assert_allclose(d0, levels[0].d, rtol=2 ** -23, atol=0)
     for lv in range(1, len(levels)):
         ref = levels[lv]
         cnt, col, v64, v32, dinv = H.level_rows(lv)
@@ -61,7 +62,7 @@ def test_hierarchy_matches_oracle(n, k, prec_name):
         assert np.all(np.abs(got - ref.vals) <= tol), float(np.max(np.abs(got - ref.vals) / scale[ref.rows]))
         np.testing.assert_array_equal(np.concatenate([v32[r, :cnt[r]] for r in range(ref.n)]),
                                       got.astype(np.float32))
-        np.testing.assert_allclose(dinv, 1.0 / ref.l1, rtol=2 ** -22, atol=0)
+        np.testing.assert_allclose(dinv, ref.d, rtol=2 ** -22, atol=0)
         # padding: (own row, 0) up to the stride
         r = int(np.argmin(cnt))
         assert np.all(col[r, cnt[r]:] == r) and np.all(v64[r, cnt[r]:] == 0.0)

@@ -46,6 +46,16 @@ def test_galerkin_equals_dense_triple_product(agg):
     np.testing.assert_allclose(Ac.dense(), want, rtol=0, atol=1e-12 * np.abs(want).max())
 
 
+def test_smoother_scaling_by_hand():
+    # a 3x3 matrix written out: row 0 diagonally strong (4 > 0.3 * 6), row 1 weak
+    # (0.5 < 0.3 * 3.5), row 2 with a negative diagonal
+    A = amg.Level(3, [0, 0, 0, 1, 1, 1, 2, 2], [0, 1, 2, 0, 1, 2, 1, 2], [4, -1, -1, 2, 0.5, -1, 3, -2])
+    assert amg.THETA == 0.3 and amg.OMEGA == 0.9
+    np.testing.assert_array_equal(A.diag, [4.0, 0.5, -2.0])
+    np.testing.assert_array_equal(A.l1, [6.0, 3.5, 5.0])
+    np.testing.assert_allclose(A.d, [0.9 / 4.0, 1.0 / 3.5, 1.0 / 5.0], rtol=1e-15)
+
+
 def test_coarse_row_sums_are_aggregated_fine_row_sums():
     _, nbr, val = _operator(2000, 16, 12)
     levels = amg.hierarchy(val, nbr, 1.0, coarsest=40)
@@ -81,7 +91,11 @@ def test_two_grid_error_propagation_operator():
     Ad = A.dense()
     P = _dense_P(n, agg)
     Ac = P.T @ Ad @ P
-    Dinv = np.diag(1.0 / np.abs(Ad).sum(axis=1))
+    # the smoother's D from the dense matrix: omega / a_ii on diagonally strong rows, l1 elsewhere
+    l1, dg = np.abs(Ad).sum(axis=1), np.diag(Ad)
+    strong = dg > amg.THETA * l1
+    assert strong.any() and not strong.all()  # both branches of the choice occur here
+    Dinv = np.diag(np.where(strong, amg.OMEGA / np.where(strong, dg, 1.0), 1.0 / l1))
     S = np.eye(n) - Dinv @ Ad
     E = S @ (np.eye(n) - P @ np.linalg.solve(Ac, P.T @ Ad)) @ S
     M = np.stack([amg.vcycle(levels, e, agg) for e in np.eye(n)], axis=1)
