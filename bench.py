@@ -37,6 +37,7 @@ sys.path.insert(0, str(ROOT))
 METRIC = "MVGD points/s (assembly+solve to 1e-8 rel) batched/served vs plain; p50/p99 ms"
 N_DEFAULT, K_DEFAULT, SEED = 1_048_576, 20, 0
 RTOL = 1e-8
+BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see run_batched)
 WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
             "6 nearest, u = 5z^3-3z, f = 13u, (I-L)u = f to 1e-8 relative residual")
 
@@ -275,7 +276,12 @@ def run_batched(args):
     """256 uneven clouds (2k-262k points, sphere / ellipsoid / torus, K 12 or 20, 4 RHS) as one batch:
     kNN per cloud on a stream pool, one batched assembly, one multigrid set-up per cloud, one persistent
     solver launch for all; points/s over the whole batch, against the same clouds solved one at a time
-    by the plain FP64 path (row scaling)."""
+    by the plain FP64 path (row scaling).
+
+    With K = 12 on uniformly random points about 0.1 % of the MVGD rows have a non-positive diagonal
+    and many of those systems do not reach 1e-8 in any solver at hand (the FP64 oracle's own BiCGSTAB,
+    GMRES(50) and multigrid-BiCGSTAB included), so every arm stops at BATCH_MAXIT iterations and the
+    line reports how many clouds (and points) converged."""
     import torch
     from paper_1603_04100_gb300 import api, build
     from paper_1603_04100_gb300 import inputs as I
@@ -292,9 +298,11 @@ def run_batched(args):
     out = {"metric": "MVGD points/s, 256-cloud batch (assembly+solve to 1e-8 rel)", "unit": "points/s",
            "n_gpus": 1, "data": "synthetic", "config": {"workload": "batched: 256 clouds, N log-uniform 2,000-262,144 "
            "(seed 2), sphere/ellipsoid/torus, K in {12, 20}, 4 RHS (x, yz, x^2-y^2, sin x e^y)", "points": total,
+           "maxit": BATCH_MAXIT,
            "rhs": sum(s[2] for s in sizes)}, "paths": {}}
     for name, prec, precond in (("fp32_refine+amg", api.FP32_REFINE, 2), ("fp64+amg", api.FP64, 2)):
-        bp = BatchPipeline(sizes, prec=prec, precond=precond, device=dev)
+        bp = BatchPipeline(sizes, prec=prec, precond=precond, device=dev, maxit=BATCH_MAXIT,
+                           inner_maxit=BATCH_MAXIT)
         for _ in range(max(1, args.warmup)):
             bp.run(pts, fs)
         torch.cuda.synchronize()
@@ -310,15 +318,21 @@ def run_batched(args):
         st = sorted({i[3] for inf in infos for i in inf})
         worst = max(i[2] for inf in infos for i in inf)
         iters = [i[0] for inf in infos for i in inf]
+        conv = [all(i[3] == 0 for i in inf) for inf in infos]
         out["paths"][name] = {"value": total / (statistics.mean(ms) * 1e-3), "ms": statistics.mean(ms),
                               "statuses": st, "worst_relres": worst, "max_iters": max(iters),
-                              "mean_iters": statistics.mean(iters)}
+                              "mean_iters": statistics.mean(iters),
+                              "converged_clouds": sum(conv), "converged_points": sum(
+                                  s[0] for s, c in zip(sizes, conv) if c),
+                              "converged_k20": sum(c for s, c in zip(sizes, conv) if s[1] == 20)}
         del bp
         torch.cuda.empty_cache()
     # plain: the same clouds one at a time, FP64 with row scaling
     t_plain = 0.0
+    conv_plain = []
     for p, pt, f in zip(probs, pts, fs):
-        pipe = Pipeline(p.pts.shape[0], p.k, p.f.shape[1], prec=api.FP64, device=dev, precond=1, rtol=RTOL)
+        pipe = Pipeline(p.pts.shape[0], p.k, p.f.shape[1], prec=api.FP64, device=dev, precond=1, rtol=RTOL,
+                        maxit=BATCH_MAXIT)
         pipe.run(pt, f)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -327,8 +341,11 @@ def run_batched(args):
         e1.record()
         torch.cuda.synchronize()
         t_plain += e0.elapsed_time(e1)
+        conv_plain.append(all(i[3] == 0 for i in api.decode_info(pipe.info)))
         del pipe
-    out["paths"]["plain_fp64_one_by_one"] = {"value": total / (t_plain * 1e-3), "ms": t_plain}
+    out["paths"]["plain_fp64_one_by_one"] = {"value": total / (t_plain * 1e-3), "ms": t_plain,
+                                             "converged_clouds": sum(conv_plain), "converged_points": sum(
+                                                 s[0] for s, c in zip(sizes, conv_plain) if c)}
     best = max((k for k in out["paths"] if k != "plain_fp64_one_by_one"), key=lambda k: out["paths"][k]["value"])
     out["value"] = out["paths"][best]["value"]
     out["path"] = best
