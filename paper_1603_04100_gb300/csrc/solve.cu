@@ -513,12 +513,14 @@ __device__ __forceinline__ void amg_spmv_row(const Prob& P, int64_t r, bool vali
     for (int sl = 0; sl < k; sl++) {
         const int64_t j = colS[sl * kSlice + lane];
         const VT w = valS[(sl + 1) * kSlice + lane];
+        VT xj[QT];
+        load_row<QT>(src, j, Q, xj);  // every right-hand side of neighbour j at once
 #pragma unroll
         for (int q = 0; q < QT; q++) {
             if (!on[q]) continue;
             // FP32: difference form (rows of L sum to zero), as in the plain flow
-            if (MIXED) acc[q] = fmaf(w, src[j * Q + q] - si[q], acc[q]);
-            else acc[q] = fma(w, src[j * Q + q], acc[q]);
+            if (MIXED) acc[q] = fmaf(w, xj[q] - si[q], acc[q]);
+            else acc[q] = fma(w, xj[q], acc[q]);
         }
     }
 #pragma unroll
@@ -1018,7 +1020,20 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                     bi[q] = (valid && inner[q]) ? (l == 0 ? (float)B0[r * Q + q] : P.vb[l][r * Q + q]) : 0.0f;
                     yi[q] = (valid && inner[q]) ? Y[r * Q + q] : 0.0f;
                 }
-                if (l == 0 && !st.wait(b, ctl.err)) continue;
+                if (l == 0) {
+                    // level 0: every right-hand side in one pass over the neighbours
+                    if (!st.wait(b, ctl.err)) continue;
+                    float ay[QT];
+#pragma unroll
+                    for (int q = 0; q < QT; q++) ay[q] = 0.0f;
+                    if (valid)
+                        a0_rows_staged<QT>(colS, w0S, lane, k, sig, yi, ay,
+                                           [&](int64_t j, float (&x)[QT]) { load_row<QT>(Y, j, Q, x); });
+#pragma unroll
+                    for (int q = 0; q < QT; q++)
+                        if (inner[q]) vdown_finish(H, 0, 1, r, valid, Q, q, bi[q] - ay[q], P.vr[0], P.vb[1], Yn, vagg);
+                    continue;
+                }
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
                     if (!inner[q]) continue;  // block-uniform
@@ -1033,7 +1048,19 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                     yi[q] = (valid && inner[q]) ? P.vy[l][r * Q + q] : 0.0f;
                     rr[q] = (valid && inner[q]) ? P.vr[l][r * Q + q] : 0.0f;
                 }
-                if (l == 0 && !st.wait(b, ctl.err)) continue;
+                if (l == 0) {
+                    // level 0: x = y + x_c + d (r - A_0 P x_c), every right-hand side in one pass
+                    if (!st.wait(b, ctl.err) || !valid) continue;
+                    float xc[QT], apx[QT];
+                    load_row<QT>(Xc, r / kAmgAgg, Q, xc);
+                    a0_rows_staged<QT>(colS, w0S, lane, k, sig, xc, apx,
+                                       [&](int64_t j, float (&x)[QT]) { load_row<QT>(Xc, j / kAmgAgg, Q, x); });
+                    const float d0 = H.lv[0].dinv[r];
+#pragma unroll
+                    for (int q = 0; q < QT; q++)
+                        if (inner[q]) X0[r * Q + q] = (VT)(yi[q] + xc[q] + d0 * (rr[q] - apx[q]));
+                    continue;
+                }
                 if (!valid && G == 1) continue;
 #pragma unroll
                 for (int q = 0; q < QT; q++) {

@@ -53,6 +53,68 @@ __device__ __forceinline__ float a0_row_staged(const int* colS, const float* w, 
     return sigma * xi - acc;
 }
 
+// Row j of an [n][Q] array into x[0..QT) (zeros past Q).  When Q == QT is 2,
+// 4 or 8 the row is one or two aligned vector loads (workspace arrays start on
+// 256 bytes), else Q scalar loads: a gather of all right-hand sides at a
+// neighbour costs one memory instruction instead of Q.
+template <int QT, typename T>
+__device__ __forceinline__ void load_row(const T* X, int64_t j, int Q, T (&x)[QT]) {
+    if constexpr (QT == 2 && sizeof(T) == 4) {
+        if (Q == 2) {
+            const float2 v = reinterpret_cast<const float2*>(X)[j];
+            x[0] = v.x;
+            x[1] = v.y;
+            return;
+        }
+    } else if constexpr ((QT == 4 || QT == 8) && sizeof(T) == 4) {
+        if (Q == QT) {
+#pragma unroll
+            for (int h = 0; h < QT / 4; h++) {
+                const float4 v = reinterpret_cast<const float4*>(X)[j * (QT / 4) + h];
+                x[4 * h] = v.x;
+                x[4 * h + 1] = v.y;
+                x[4 * h + 2] = v.z;
+                x[4 * h + 3] = v.w;
+            }
+            return;
+        }
+    } else if constexpr (QT >= 2 && QT <= 8 && (QT & (QT - 1)) == 0 && sizeof(T) == 8) {
+        if (Q == QT) {
+#pragma unroll
+            for (int h = 0; h < QT / 2; h++) {
+                const double2 v = reinterpret_cast<const double2*>(X)[j * (QT / 2) + h];
+                x[2 * h] = v.x;
+                x[2 * h + 1] = v.y;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < QT; q++) x[q] = q < Q ? X[j * Q + q] : T(0);
+}
+
+// Level-0 products of every right-hand side from a staged slice (colS [k][32]
+// columns, w [k+1][32] weights, slot 0 = the row itself): out[q] = sigma xi[q]
+// - sum_s w_s (x_j[q] - xi[q]), the neighbours' rows read by `xrow(j, x)`.
+// Each q's operations are those of a0_row_staged, in the same order.
+template <int QT, typename XR>
+__device__ __forceinline__ void a0_rows_staged(const int* colS, const float* w, int lane, int k, float sigma,
+                                               const float (&xi)[QT], float (&out)[QT], XR&& xrow) {
+    float acc[QT];
+#pragma unroll
+    for (int q = 0; q < QT; q++) acc[q] = 0.0f;
+#pragma unroll 4
+    for (int s = 0; s < k; s++) {
+        float xj[QT];
+        xrow((int64_t)colS[s * kSlice + lane], xj);
+        const float ws = w[(s + 1) * kSlice + lane];
+#pragma unroll
+        for (int q = 0; q < QT; q++) acc[q] = fmaf(ws, xj[q] - xi[q], acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < QT; q++) out[q] = sigma * xi[q] - acc[q];
+}
+
 // Level-l (>= 1) product with the explicit Galerkin matrix, row r taken by the
 // G lanes of its group (G a power of two <= 32, groups aligned in the warp):
 // lane `sub` sums slots sub, sub + G, ... and the group adds its partials by a
@@ -101,17 +163,10 @@ __device__ __forceinline__ float agg_sum(float v, int G, float* agg) {
 // aggregate (the first lane of its first row).  `a0(xi, xv)` is the level-0
 // product (from global memory or a staged slice).  With G >= 8 every thread
 // of the block calls it (see agg_sum).
-template <typename YOF, typename A0>
-__device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int G, int64_t r, bool valid, int Q, int q,
-                                          float b, float yi, YOF&& y_of, float* R, float* Bn, float* Yn, A0&& a0,
-                                          float* agg) {
+// The rest of a down step once the row's residual res = b - A_l y is known.
+__device__ __forceinline__ void vdown_finish(const AmgHeader& H, int l, int G, int64_t r, bool valid, int Q, int q,
+                                             float res, float* R, float* Bn, float* Yn, float* agg) {
     const bool lead = (lane_id() & (G - 1)) == 0;
-    float res = 0.0f;
-    if (l == 0) {
-        if (valid) res = b - a0(yi, y_of);
-    } else {
-        res = b - al_row(H.lv[l], r, valid, G, yi, y_of);
-    }
     if (!valid) res = 0.0f;  // rows past the end contribute 0
     if (valid && lead) R[r * Q + q] = res;
     const float bc = agg_sum(res, G, agg);
@@ -120,6 +175,19 @@ __device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int G, int6
         Bn[I * Q + q] = bc;
         if (Yn) Yn[I * Q + q] = H.lv[l + 1].dinv[I] * bc;
     }
+}
+
+template <typename YOF, typename A0>
+__device__ __forceinline__ void vdown_row(const AmgHeader& H, int l, int G, int64_t r, bool valid, int Q, int q,
+                                          float b, float yi, YOF&& y_of, float* R, float* Bn, float* Yn, A0&& a0,
+                                          float* agg) {
+    float res = 0.0f;
+    if (l == 0) {
+        if (valid) res = b - a0(yi, y_of);
+    } else {
+        res = b - al_row(H.lv[l], r, valid, G, yi, y_of);
+    }
+    vdown_finish(H, l, G, r, valid, Q, q, res, R, Bn, Yn, agg);
 }
 
 // Up step of level l: x_l = y_l + P x_{l+1} + d_l (r_l - A_l P x_{l+1}), for
