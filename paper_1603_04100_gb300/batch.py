@@ -5,6 +5,7 @@ A batch of clouds (any sizes, K and number of right-hand sides each) runs as:
     small clouds overlap instead of queueing;
   * assembly: ONE launch over (cloud, 32-row slice) work items
     (mvgd_assemble_batch);
+  * multigrid set-up (precond 2): each cloud's hierarchy on the stream pool;
   * solve: every cloud is a request with its own solver state; ONE persistent
     launch (mvgd_iterate) advances all of them to convergence; requests that
     finish early cost nothing while the rest iterate.
@@ -23,6 +24,7 @@ import torch
 
 from . import _lib as LB
 from . import api
+from .serve import amg_setup_kernels
 
 
 @dataclass
@@ -116,10 +118,23 @@ class BatchPipeline:
         s = api._stream(main)
         LB.check("mvgd_assemble_batch", L.mvgd_assemble_batch(items, len(self.slots), self.rule, vp(self.bad_rows),
                                                                vp(self.asm_ws), self.asm_ws.numel(), s))
+        if self.precond == LB.PRECOND_AMG:
+            # the hierarchies on the stream pool: each set-up is a chain of small
+            # launches (the coarsest inverse is one block), so clouds overlap
+            built = torch.cuda.Event()
+            built.record(main)
+            for i, slot in enumerate(self.slots):
+                st = self.streams[i % len(self.streams)]
+                st.wait_event(built)
+                c = slot.op.cstruct()
+                LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(slot.amg_ws), slot.amg_ws.numel(),
+                                                             api._stream(st)))
+            for st in self.streams:
+                ev = torch.cuda.Event()
+                ev.record(st)
+                main.wait_event(ev)
         for slot, f, opts in zip(self.slots, f_list, self._opts):
             c = slot.op.cstruct()
-            if slot.amg_ws is not None:
-                LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(slot.amg_ws), slot.amg_ws.numel(), s))
             LB.check("mvgd_request_init", L.mvgd_request_init(vp(slot.req_ws), slot.req_ws.numel(), C.byref(c),
                                                                slot.nrhs, 1.0, vp(f), None, C.byref(opts), s))
         LB.check("mvgd_iterate", L.mvgd_iterate(self._reqs, len(self.slots), self.prec, self.precond, self.budget,
@@ -149,4 +164,5 @@ class BatchPipeline:
         per_cloud_knn = 11
         return (len(self.slots) * (per_cloud_knn + 1 + 3 + 2)  # knn, inverse order, init (2 gathers+1), finish (2)
                 + 1 + (len(self.slots) + 47) // 48              # batched assembly + descriptor uploads
-                + (len(self.slots) + 255) // 256 + 3)           # iterate: tables, count, solver, exit marks
+                + (len(self.slots) + 255) // 256 + 3            # iterate: tables, count, solver, exit marks
+                + (sum(amg_setup_kernels(s.n) for s in self.slots) if self.precond == LB.PRECOND_AMG else 0))

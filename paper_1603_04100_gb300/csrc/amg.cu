@@ -115,7 +115,11 @@ constexpr int kPerLane = kAmgAgg * kAmgStride / kWarp;  // entries a lane holds 
 // Level l+1 from level l, one warp per coarse row I: gather the entries of
 // the aggregate's rows, then emit distinct aggregate columns in increasing
 // order, each with the FP64 sum of its entries (per-lane sums in entry order,
-// then a butterfly over the warp: the same order on every run).
+// then a butterfly over the warp: the same order on every run).  Each lane
+// first sorts its entries by (column, slot) and adds up its equal columns
+// once, so the merge over columns moves values instead of adding them: the
+// GPU's FP64 rate made those predicated adds (one per entry and column) the
+// kernel's cost.
 __global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
     const AmgHeader& H = *Hp;
     const AmgLevel& F = H.lv[l];
@@ -152,6 +156,31 @@ __global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
                 v[t] = F.val64[idx];
             }
         }
+        // sort the lane's entries by (column, slot): an odd-even transposition network
+        int tt[kPerLane];
+#pragma unroll
+        for (int t = 0; t < kPerLane; t++) tt[t] = t;
+#pragma unroll
+        for (int ph = 0; ph < kPerLane; ph++)
+#pragma unroll
+            for (int i = ph & 1; i + 1 < kPerLane; i += 2) {
+                const bool sw = key[i] > key[i + 1] || (key[i] == key[i + 1] && tt[i] > tt[i + 1]);
+                const int ka = key[i], ta = tt[i];
+                const double va = v[i];
+                key[i] = sw ? key[i + 1] : ka;
+                tt[i] = sw ? tt[i + 1] : ta;
+                v[i] = sw ? v[i + 1] : va;
+                key[i + 1] = sw ? ka : key[i + 1];
+                tt[i + 1] = sw ? ta : tt[i + 1];
+                v[i + 1] = sw ? va : v[i + 1];
+            }
+        // the lane's sum of each column, in slot order, left on its last entry
+#pragma unroll
+        for (int t = 1; t < kPerLane; t++)
+            if (key[t] != INT_MAX && key[t] == key[t - 1]) {
+                v[t] = v[t - 1] + v[t];
+                key[t - 1] = INT_MAX;
+            }
         const int64_t ob = (I / kSlice) * (int64_t)(kSlice * kAmgStride) + (I % kSlice);
         int out = 0;
         double l1 = 0.0, rsum = 0.0, diag = 0.0;
@@ -163,11 +192,11 @@ __global__ void k_amg_coarsen(const AmgHeader* Hp, OpView O, int l) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
             if (m == INT_MAX) break;
-            double part = 0.0;
+            double part = 0.0;  // at most one entry of the lane holds column m now
 #pragma unroll
             for (int t = 0; t < kPerLane; t++)
                 if (key[t] == m) {
-                    part += v[t];
+                    part = v[t];
                     key[t] = INT_MAX;
                 }
             const double tot = warp_sum(part);

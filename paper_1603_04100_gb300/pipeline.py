@@ -66,7 +66,7 @@ class Pipeline:
             while m > LB.AMG_COARSEST:
                 m = (m + LB.AMG_AGG - 1) // LB.AMG_AGG
                 lv += 1
-            k += 4 + 2 * (lv - 1)                    # hierarchy set-up
+            k += 9 + 2 * (lv - 1)                    # hierarchy set-up (with the Newton-Schulz products)
             k += (lv - 2 if lv > 2 else 0) + 1       # level and coarsest chunk tables
         return k
 

@@ -86,14 +86,16 @@ def amg_levels(n: int) -> int:
 
 
 def amg_setup_kernels(n: int) -> int:
-    """Kernels mvgd_amg_setup launches: header, level 0, two per coarser level, dense, inverse."""
-    return 4 + 2 * (amg_levels(n) - 1)
+    """Kernels mvgd_amg_setup launches: header, level 0, two per coarser level, dense, inverse, promotion
+    and four Newton-Schulz products."""
+    return 9 + 2 * (amg_levels(n) - 1)
 
 
 class Server:
     def __init__(self, device="cuda:0", *, hbm_budget: float = 120e9, prec: int = api.FP32_REFINE,
                  epoch_iters: int = 32, rtol: float = 1e-8, inner_rtol: float = 1e-5, precond: int = 1,
-                 maxit: int = 200000, max_active: int = 1024, max_points: int = 1 << 21, max_k: int = 31):
+                 maxit: int = 200000, max_active: int = 1024, max_points: int = 1 << 21, max_k: int = 31,
+                 pool_streams: int = 4):
         self.device = torch.device(device)
         self.budget = float(hbm_budget)
         self.prec = prec
@@ -104,8 +106,10 @@ class Server:
         self.rule = LB.DeltaRule(api.DELTA_MEAN_NN, 6, 1.0)
         L = LB.load()
         self.stream = torch.cuda.Stream(device=self.device)
-        self.knn_ws = torch.empty(L.mvgd_knn_workspace_bytes(max_points, max_k), dtype=torch.uint8,
-                                  device=self.device)
+        # admission work of different requests (kNN, multigrid set-up) overlaps on a pool
+        self.pool = [torch.cuda.Stream(device=self.device) for _ in range(max(1, pool_streams))]
+        self.knn_ws = [torch.empty(L.mvgd_knn_workspace_bytes(max_points, max_k), dtype=torch.uint8,
+                                   device=self.device) for _ in self.pool]
         self.ctl_bytes = L.mvgd_iterate_workspace_bytes(max_active, 1 << 31)
         self.ctl_ws = torch.empty(self.ctl_bytes, dtype=torch.uint8, device=self.device)
         self.done_dev = torch.zeros(max_active, dtype=torch.int32, device=self.device)
@@ -124,16 +128,27 @@ class Server:
         s = api._stream(self.stream)
         live = []
         with torch.cuda.stream(self.stream):
+            # device buffers and uploads on the server's stream (which owns the memory),
+            # then each request's kNN on a pool stream
+            staged = []
             for r in reqs:
-                n, k, q = r.n, r.k, r.nrhs
-                if n > self.knn_ws.numel():  # pragma: no cover - guarded by max_points
+                n, k = r.n, r.k
+                if L.mvgd_knn_workspace_bytes(n, k) > self.knn_ws[0].numel():  # pragma: no cover - max_points
                     raise ValueError("cloud larger than the server's kNN workspace")
-                pts = torch.from_numpy(r.pts).to(self.device, non_blocking=True)
-                f = torch.from_numpy(np.ascontiguousarray(r.f)).to(self.device, non_blocking=True)
-                nbr = torch.empty((n, k), dtype=torch.int32, device=self.device)
-                order = torch.empty(n, dtype=torch.int32, device=self.device)
-                LB.check("mvgd_knn", L.mvgd_knn(vp(pts), n, k, vp(nbr), vp(order), 0.0, vp(self.knn_ws),
-                                                 self.knn_ws.numel(), s))
+                staged.append((torch.from_numpy(r.pts).to(self.device, non_blocking=True),
+                               torch.from_numpy(np.ascontiguousarray(r.f)).to(self.device, non_blocking=True),
+                               torch.empty((n, k), dtype=torch.int32, device=self.device),
+                               torch.empty(n, dtype=torch.int32, device=self.device)))
+            uploaded = torch.cuda.Event()
+            uploaded.record(self.stream)
+            for p in self.pool:
+                p.wait_event(uploaded)
+            for i, (r, (pts, f, nbr, order)) in enumerate(zip(reqs, staged)):
+                n, k, q = r.n, r.k, r.nrhs
+                ps = self.pool[i % len(self.pool)]
+                ws_knn = self.knn_ws[i % len(self.pool)]
+                LB.check("mvgd_knn", L.mvgd_knn(vp(pts), n, k, vp(nbr), vp(order), 0.0, vp(ws_knn), ws_knn.numel(),
+                                                 api._stream(ps)))
                 self.launches += 11
                 col, val, lo = api.ell_alloc(n, k, self.prec, self.device)
                 op = api.Operator(n, k, self.prec, col, val, lo, order)
@@ -148,6 +163,10 @@ class Server:
                                         self.opts.max_outer, self.precond, C.c_void_p(amg.data_ptr()))
                 live.append(_Live(r, request_bytes(n, k, q, self.prec, self.precond), pts, f, nbr, order, op, ws, u,
                                   info, amg, opts))
+            for p in self.pool:
+                ev = torch.cuda.Event()
+                ev.record(p)
+                self.stream.wait_event(ev)
             items = (LB.AssembleItem * len(live))()
             ns = (C.c_int64 * len(live))(*[x.req.n for x in live])
             aws = torch.empty(L.mvgd_assemble_batch_workspace_bytes(ns, len(live)), dtype=torch.uint8,
@@ -157,11 +176,22 @@ class Server:
             LB.check("mvgd_assemble_batch", L.mvgd_assemble_batch(items, len(live), self.rule, None, vp(aws),
                                                                    aws.numel(), s))
             self.launches += 1 + len(live) + (len(live) + 47) // 48
+            if self.precond == LB.PRECOND_AMG:
+                built = torch.cuda.Event()
+                built.record(self.stream)
+                for i, x in enumerate(live):
+                    ps = self.pool[i % len(self.pool)]
+                    ps.wait_event(built)
+                    c = x.op.cstruct()
+                    LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(x.amg), x.amg.numel(),
+                                                                 api._stream(ps)))
+                    self.launches += amg_setup_kernels(x.req.n)
+                for p in self.pool:
+                    ev = torch.cuda.Event()
+                    ev.record(p)
+                    self.stream.wait_event(ev)
             for x in live:
                 c = x.op.cstruct()
-                if x.amg is not None:
-                    LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(x.amg), x.amg.numel(), s))
-                    self.launches += amg_setup_kernels(x.req.n)
                 LB.check("mvgd_request_init", L.mvgd_request_init(vp(x.ws), x.ws.numel(), C.byref(c), x.req.nrhs,
                                                                    1.0, vp(x.f), None, C.byref(x.opts), s))
                 self.launches += 3 + (1 if self.precond == LB.PRECOND_ROWSCALE else 0)

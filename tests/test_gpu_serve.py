@@ -23,28 +23,31 @@ def _requests():
     return requests_from_trace(specs)
 
 
-def _solo(dev, r):
+def _solo(dev, r, precond):
     from paper_1603_04100_gb300 import api
     pts = torch.from_numpy(r.pts).to(dev)
     nbr, order = api.knn(pts, r.k, want_order=True)
     op = api.assemble(pts, nbr, prec=api.FP32_REFINE, order=order)
-    res = api.solve(op, torch.from_numpy(np.ascontiguousarray(r.f)).to(dev), rtol=1e-8, precond=1)
+    res = api.solve(op, torch.from_numpy(np.ascontiguousarray(r.f)).to(dev), rtol=1e-8, precond=precond)
     return res.u.cpu().numpy(), res
 
 
-def test_serving_joins_and_identity(dev):
+@pytest.mark.parametrize("precond", [1, 2])
+def test_serving_joins_and_identity(dev, precond):
+    # precond 2: each admitted request's hierarchy is built on the server's stream
+    # pool; the result still equals the request solved alone, bit for bit
     from paper_1603_04100_gb300.serve import Server, request_bytes
     reqs = _requests()
-    big = sorted(request_bytes(r.n, r.k, r.nrhs, 1) for r in reqs)
+    big = sorted(request_bytes(r.n, r.k, r.nrhs, 1, precond) for r in reqs)
     budget = sum(big[-4:])  # room for about four requests at once: later ones must wait
-    srv = Server(dev, hbm_budget=budget, epoch_iters=16, max_points=1 << 16, max_k=20)
+    srv = Server(dev, hbm_budget=budget, epoch_iters=16, max_points=1 << 16, max_k=20, precond=precond)
     stats = srv.serve(reqs)
     assert stats["statuses"] == [0], stats
     assert stats["joins"] > 0 and stats["max_concurrent"] >= 2, stats
     assert stats["waited_request_epochs"] > 0, stats
     assert srv.used == 0
     for r in reqs:
-        u, res = _solo(dev, r)
+        u, res = _solo(dev, r, precond)
         assert np.array_equal(u, r.u), r.rid
         assert [i[0] for i in r.info] == res.iters
     assert stats["p99_ms"] >= stats["p50_ms"] > 0
