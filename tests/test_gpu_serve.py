@@ -39,7 +39,9 @@ def test_serving_joins_and_identity(dev, precond):
     from paper_1603_04100_gb300.serve import Server, request_bytes
     reqs = _requests()
     big = sorted(request_bytes(r.n, r.k, r.nrhs, 1, precond) for r in reqs)
-    budget = sum(big[-4:])  # room for about four requests at once: later ones must wait
+    # room for a few requests at once, so that later ones must wait (multigrid
+    # requests finish in fewer epochs: less room)
+    budget = sum(big[-4:]) if precond == 1 else sum(big[-2:])
     srv = Server(dev, hbm_budget=budget, epoch_iters=16, max_points=1 << 16, max_k=20, precond=precond)
     stats = srv.serve(reqs)
     assert stats["statuses"] == [0], stats
