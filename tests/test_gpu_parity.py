@@ -176,6 +176,30 @@ def test_spmv_mixed_modes(dev, nrhs):
     assert np.all(np.abs(got32 - want32) <= bound), (np.abs(got32 - want32) / bound).max()
 
 
+@pytest.mark.parametrize("k,nrhs", [(9, 1), (12, 2), (24, 1), (31, 2)])
+def test_spmv_every_k_path(dev, k, nrhs):
+    # K in {12, 16, 20, 24} runs kernels with K fixed at compile time, any other K
+    # the run-time-K kernel: both against the oracle, FP64 and FP32 difference form
+    api = _api()
+    p = I.random_sphere(5003, 11 + k)  # 5003: a ragged last slice
+    x = _random_x(len(p), nrhs, 3)
+    op, nbr, val, st, dg = _assemble_both(dev, p, k, api.FP64)
+    assert int(st.max()) == 0  # no rank-deficient fit in these clouds
+    want = oracle.spmv(val, nbr, x, sigma=1.0)
+    got = api.spmv(op, torch.from_numpy(x).to(dev)).cpu().numpy()
+    scale = (np.abs(val[:, :1]) + np.abs(val[:, 1:]).sum(1, keepdims=True)) * np.abs(x).max()
+    assert np.all(np.abs(got - want) <= 1e-12 * scale)
+    op32, nbr32, val32, _, _ = _assemble_both(dev, p, k, api.FP32_REFINE)
+    x32 = x.astype(np.float32)
+    xd = x32.astype(np.float64)
+    got32 = api.spmv(op32, torch.from_numpy(x32).to(dev), mode=api.SPMV_F32).cpu().numpy().astype(np.float64)
+    want32 = oracle.spmv(val32, nbr32, xd, sigma=1.0)
+    diff_scale = np.stack([(np.abs(val32[:, 1:]) * np.abs(xd[nbr32, q] - xd[:, q:q + 1])).sum(1)
+                           for q in range(nrhs)], 1)
+    bound = 64 * 2.0 ** -24 * (diff_scale + np.abs(xd)) + 1e-30
+    assert np.all(np.abs(got32 - want32) <= bound), (np.abs(got32 - want32) / bound).max()
+
+
 def _solve_both(dev, pr, prec, rtol, precond=0, order=True):
     api = _api()
     pt = torch.from_numpy(pr.pts).to(dev)
