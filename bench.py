@@ -8,7 +8,7 @@ sphere, K = 20, u = 5z^3 - 3z, f = 13u (synthetic, seeded).
 One JSON line on rank 0.  A step is one pass of the whole path over one cloud:
 kNN -> MVGD assembly -> solve.  The timed path is the FP32 + FP64-refinement
 one; the plain FP64 path (same kNN, same preconditioner, FP64 assembly, FP64
-Krylov) is timed beside it.  L2 is flushed (256 MiB write) before every step,
+Krylov) is timed beside it.  L2 is flushed (1 GiB write) before every step,
 outside the per-step CUDA-event windows.  With N > 1 (torchrun) every rank
 solves its own replica of the cloud (weak scaling, no collective on the data
 path); the reported time is the max over ranks.
@@ -162,7 +162,10 @@ def spmv_roofline(results, n, k, flush, stream, peak, peak_kind, reps: int = 20)
     """mvgd_spmv timed alone: y = sigma x - L x, one RHS, per launch (CUDA events on the
     launching stream, L2 flushed before each launch).  Algorithmic bytes per row:
     FP32 difference form col 4k + val 4k (the self weight is implied) + x_i + y_i = 8k + 8;
-    FP64 col 4k + val 8(k+1) + x_i + y_i = 12k + 24 (neighbour gathers hit L2)."""
+    FP64 col 4k + val 8(k+1) + x_i + y_i = 12k + 24 (neighbour gathers hit L2).
+    The flush before each launch writes 1 GiB (about 0.15 ms of device time), longer than
+    the host needs to enqueue the product, so the event pair brackets the kernel and not
+    the host's launch latency (a 35 us kernel behind a 40 us flush read as 45 us)."""
     import torch
     from paper_1603_04100_gb300 import api
     out = {}
@@ -418,7 +421,7 @@ def main():
     pts = torch.from_numpy(pr.pts).to(dev)
     f = torch.from_numpy(pr.f).to(dev)
     stream = torch.cuda.Stream(device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.empty(1 << 30, dtype=torch.uint8, device=dev)  # also outlasts the host's first launches
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -436,16 +439,17 @@ def main():
         for _ in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
                 ev[0].record(stream)
                 pipe.run_staged(pts, f, ev)
-                ev[3].record(stream)
+                ev[4].record(stream)
             rec.append(ev)
         barrier()
         wall = time.perf_counter() - t_wall
         out = []
-        for ev in rec:
-            out.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])))
+        for ev in rec:  # kNN, assembly, solve stage (set-up + solver), solver call alone
+            out.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[4]),
+                        ev[3].elapsed_time(ev[4])))
         return out, wall
 
     def max_over_ranks(ms):
@@ -471,7 +475,7 @@ def main():
             rec, _ = timed_runs(pipe, args.steps, args.warmup)
             info = pipe.decode()[0]
             u = pipe.u[:, 0].double().cpu().numpy()
-            step_ms = [sum(r) for r in rec]
+            step_ms = [r[0] + r[1] + r[2] for r in rec]
             results[name] = {"pipe": pipe, "rec": rec, "info": info, "u": u, "step_ms": step_ms,
                              "ms": max_over_ranks(statistics.mean(step_ms)), "mixed": prec == api.FP32_REFINE,
                              "amg": precond == 2}
@@ -488,8 +492,9 @@ def main():
     info, rec, step_ms = R["info"], R["rec"], R["step_ms"]
     err_exact = float(abs(R["u"] - pr.u_exact[:, 0]).max())
 
-    # roofline of the dominant kernel: the persistent solver of the headline path
-    solve_ms = statistics.mean(r[2] for r in rec)
+    # roofline of the dominant kernel: the persistent solver of the headline path, timed
+    # as the mvgd_solve call (request set-up, the k_solve launch, the scatter of u)
+    solve_ms = statistics.mean(r[3] for r in rec)
     mixed_best = R["mixed"]
     bytes_solve = solver_bytes_per_row(k, mixed_best, info[0], info[1], R.get("amg_coarse")) * n
     peak, peak_kind = measured_peaks()
@@ -499,7 +504,8 @@ def main():
                 "kernel": "k_solve (persistent BiCGSTAB, " + ("FP32 inner + FP64 refinement" if mixed_best else "FP64")
                           + (", multigrid V-cycle preconditioner)" if R["amg"] else ", row scaling)"),
                 "peak_kind": f"hbm_gbs of {peak_kind}", "bytes_per_launch": bytes_solve, "launch_ms": solve_ms,
-                "note": "launch_ms is the solve stage: multigrid set-up (if any) + the persistent solver"}
+                "note": "launch_ms is the mvgd_solve call: the k_solve launch plus its request set-up and "
+                        "solution scatter (the multigrid set-up is timed apart, in stage_ms.amg_setup)"}
 
     def summary(nm):
         r = results[nm]
@@ -512,7 +518,9 @@ def main():
                 "err_exact_inf": float(abs(r["u"] - pr.u_exact[:, 0]).max()),
                 "stage_ms": {"knn": statistics.mean(x[0] for x in r["rec"]),
                              "assemble": statistics.mean(x[1] for x in r["rec"]),
-                             "solve": statistics.mean(x[2] for x in r["rec"])}}
+                             "solve": statistics.mean(x[2] for x in r["rec"]),
+                             "amg_setup": statistics.mean(x[2] - x[3] for x in r["rec"]),
+                             "solver": statistics.mean(x[3] for x in r["rec"])}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
@@ -520,12 +528,13 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64" if mixed_best else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "k": k, "rtol": RTOL,
                    "precond": "multigrid V(1,1)-cycle (aggregation)" if R["amg"] else "row abs-sum scaling",
-                   "path": best, "l2": "flushed before every step (256 MiB write), outside the step events",
+                   "path": best, "l2": "flushed before every step (1 GiB write), outside the step events",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "p50_ms": statistics.median(step_ms),
         "p99_ms": sorted(step_ms)[min(len(step_ms) - 1, math.ceil(0.99 * len(step_ms)) - 1)],
         "stage_ms": {"knn": statistics.mean(r[0] for r in rec), "assemble": statistics.mean(r[1] for r in rec),
-                     "solve": solve_ms},
+                     "solve": statistics.mean(r[2] for r in rec),
+                     "amg_setup": statistics.mean(r[2] - r[3] for r in rec), "solver": solve_ms},
         "iters": info[0], "outer": info[1], "relres": info[2], "solve_status": info[3],
         "err_exact_inf": err_exact,
         "gpu_launches": R["pipe"].kernels_per_run * args.steps + args.steps,  # + one flush per step

@@ -75,7 +75,8 @@ class Pipeline:
         return self.run_staged(pts, f, None)
 
     def run_staged(self, pts: torch.Tensor, f: torch.Tensor, events=None) -> torch.Tensor:
-        """As run(); events[1] / events[2] (if given) are recorded after kNN / assembly."""
+        """As run(); events[1] / events[2] / events[3] (if given) are recorded after kNN /
+        assembly / the multigrid set-up (right after assembly without one)."""
         L = LB.load()
         st = self.stream if self.stream is not None else torch.cuda.current_stream()
         s = api._stream(st)
@@ -94,6 +95,8 @@ class Pipeline:
             self.u.zero_()
         if self.ws_amg is not None:
             LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(self.ws_amg), self.ws_amg.numel(), s))
+        if events is not None and len(events) > 4:
+            events[3].record(st)
         LB.check("mvgd_solve", L.mvgd_solve(C.byref(c), self.nrhs, 1.0, vp(f), vp(self.u), C.byref(self.opts),
                                              vp(self.info), None, vp(self.ws_solve), self.ws_solve.numel(), s))
         return self.info
