@@ -195,6 +195,29 @@ def spmv_roofline(results, n, k, flush, stream, peak, peak_kind, reps: int = 20)
     return out
 
 
+def row_sign_stats(pts, pipe, k, flush, stream):
+    """Sec. 3.2 / Sec. 4.1 on the bench cloud: the share of rows with the M-matrix sign
+    pattern (mvgd_row_signs) for the MVGD rows and for the plain least-squares comparator,
+    and the device time of the comparator's assembly (same kernel, variant ROW_LS)."""
+    import torch
+    from paper_1603_04100_gb300 import api
+    out = {}
+    with torch.cuda.stream(stream):
+        mv = api.row_signs(pipe.op, stream=stream)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ls = api.assemble(pts, pipe.nbr, prec=api.FP64, order=pipe.order, variant=api.ROW_LS, stream=stream)
+        e1.record(stream)
+        lsc = api.row_signs(ls, stream=stream)
+    stream.synchronize()
+    for nm, c in (("mvgd", mv), ("least_squares", lsc)):
+        out[nm] = {"m_pattern_frac": c["m_pattern_rows"] / c["rows"], "negative_weights": c["negative_weights"],
+                   "nonneg_self_rows": c["nonneg_self_rows"]}
+    out["least_squares_assembly_ms"] = e0.elapsed_time(e1)
+    return out
+
+
 def amg_coarse_bytes(H, n: int) -> float:
     """Bytes per fine row that one V-cycle moves on levels >= 1: per level, down
     and up read each stored entry (int32 column + FP32 value) once, plus about
@@ -554,6 +577,7 @@ def main():
     # a6 on its own: the standalone operator application on the assembled 1M operators
     # (FP32 difference form on hi weights, FP64 standard form), L2 flushed before each launch
     line["spmv"] = spmv_roofline(results, n, k, flush, stream, peak, peak_kind)
+    line["row_signs"] = row_sign_stats(pts, mixed, k, flush, stream)
 
     if not args.no_e2e:
         pts_h = torch.from_numpy(pr.pts).pin_memory()

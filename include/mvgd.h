@@ -106,10 +106,20 @@ mvgd_status mvgd_knn_noalloc(const double *pts, int64_t n, int32_t k, int32_t *n
 typedef enum { MVGD_DELTA_QUARTER_RANGE = 0, MVGD_DELTA_MEAN_NN = 1 } mvgd_delta_kind;
 
 typedef struct {
-    int32_t kind;  /* mvgd_delta_kind */
-    int32_t m;     /* MEAN_NN only */
-    double scale;  /* 1.0 = the paper's rule */
+    int32_t kind;     /* mvgd_delta_kind */
+    int32_t m;        /* MEAN_NN only */
+    double scale;     /* 1.0 = the paper's rule */
+    int32_t variant;  /* mvgd_row_variant; 0 (zero-initialised) = MVGD */
+    int32_t reserved; /* 0 */
 } mvgd_delta_rule;
+
+/* Which row the assembly forms.  MVGD_ROW_MVGD is the method (Sec. 3.1).
+ * MVGD_ROW_LS is the comparator of Sec. 2: the LB of the local least-squares
+ * quadratic itself, w = A1 U_x + A2 U_y + A3 U_xx + A4 U_xy + A5 U_yy from the
+ * fit's derivatives at the origin, without the centre value substituted on the
+ * virtual grid.  Both rows sum to zero; they differ by
+ * 2 (A3 + A5) / h^2 (P_00 - e_self). */
+typedef enum { MVGD_ROW_MVGD = 0, MVGD_ROW_LS = 1 } mvgd_row_variant;
 
 typedef enum {
     MVGD_FP64 = 0,        /* weights FP64; plain FP64 SpMV and Krylov */
@@ -172,6 +182,18 @@ size_t mvgd_assemble_batch_workspace_bytes(const int64_t *n, int32_t count);
 mvgd_status mvgd_assemble_batch(const mvgd_assemble_item *items, int32_t count, mvgd_delta_rule rule,
                                 int32_t *bad_rows, void *workspace, size_t workspace_bytes,
                                 mvgd_stream_t stream);
+
+/* Sign pattern of an assembled operator's rows (Sec. 3.2 and Sec. 4.1).  The
+ * rows sum to zero, so a row whose K neighbour weights are all >= 0 makes
+ * sigma I - L diagonally dominant with non-positive off-diagonal entries: the
+ * M-matrix pattern the paper's MVGD is built to favour over the plain
+ * least-squares row.  counts: DEVICE int64 [3] (8-byte aligned), overwritten:
+ *   [0] rows whose neighbour weights are all >= 0,
+ *   [1] neighbour weights < 0, over all rows,
+ *   [2] rows whose self weight w_0 is >= 0 (a Laplacian row has w_0 < 0).
+ * Weights are FP64, or hi + lo evaluated in FP64.  Padding rows are not counted.
+ * Asynchronous; MVGD_EINVAL on a null pointer or out-of-range sizes. */
+mvgd_status mvgd_row_signs(const mvgd_ell *L, int64_t *counts, mvgd_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Operator application (the product every Krylov step repeats, Sec. 3.1 and

@@ -15,6 +15,7 @@ the paper they follow):
 * ``spmv``, ``bicgstab``, ``gmres``: y = alpha (sigma x - L x) + beta y and
   solvers of (sigma I - L) u = f.
 * ``line_weights``: the 1-D worked example of Sec. 3.2.
+* ``row_sign_counts``: the M-matrix sign pattern of rows (Sec. 3.2, Sec. 4.1).
 * ``normal_matrix``: the 6x6 normal-equation matrix of Sec. 2 as printed.
 """
 from __future__ import annotations
@@ -164,6 +165,17 @@ def line_weights(xs, c: int, h: float, variant: int = VARIANT_MVGD) -> np.ndarra
     if lib().or_line_weights(_ptr(xs), xs.shape[0], c, h, variant, _ptr(w)) != 0:
         raise ValueError("or_line_weights: bad arguments")
     return w
+
+
+def row_sign_counts(val) -> tuple:
+    """Sign pattern of MVGD rows [n][k+1] (slot 0 = the point itself), Sec. 3.2 and
+    Sec. 4.1: (rows whose neighbour weights are all >= 0 -- with zero row sums the
+    M-matrix pattern of sigma I - L --, neighbour weights < 0, rows whose self
+    weight is >= 0)."""
+    val = _f64(val)
+    nbrs = val[:, 1:]
+    return (int(np.count_nonzero(np.all(nbrs >= 0.0, axis=1))), int(np.count_nonzero(nbrs < 0.0)),
+            int(np.count_nonzero(val[:, 0] >= 0.0)))
 
 
 def normal_matrix(x, y) -> np.ndarray:

@@ -15,6 +15,7 @@ LIB_PATH = Path(__file__).resolve().parent / "_build" / "libmvgd.so"
 # status codes (mvgd_status)
 OK, EINVAL, EWORKSPACE, EDEGENERATE, ENOCONV, EBREAKDOWN, ENONFINITE, ECANCELLED, ETIMEOUT, ECUDA = range(10)
 DELTA_QUARTER_RANGE, DELTA_MEAN_NN = 0, 1
+ROW_MVGD, ROW_LS = 0, 1  # mvgd_row_variant
 FP64, FP32_REFINE = 0, 1
 ELL_COL, ELL_VAL, ELL_VAL_LO = 0, 1, 2
 SPMV_F64, SPMV_F32, SPMV_F64_HILO = 0, 1, 2
@@ -26,13 +27,15 @@ EXPORTS = (
     "mvgd_request_finish", "mvgd_assemble_batch_workspace_bytes", "mvgd_assemble_batch", "mvgd_request_poll",
     "mvgd_knn_noalloc", "mvgd_amg_workspace_bytes", "mvgd_amg_setup", "mvgd_amg_describe",
     "mvgd_amg_apply_workspace_bytes", "mvgd_amg_apply", "mvgd_trace_enable", "mvgd_trace_read",
+    "mvgd_row_signs",
 )
 PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
 AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
 
 
 class DeltaRule(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("m", C.c_int32), ("scale", C.c_double)]
+    _fields_ = [("kind", C.c_int32), ("m", C.c_int32), ("scale", C.c_double), ("variant", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Ell(C.Structure):
@@ -141,6 +144,8 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_trace_enable.restype = C.c_int
     L.mvgd_trace_read.argtypes = [C.POINTER(C.c_uint64), C.c_int32]
     L.mvgd_trace_read.restype = C.c_int32
+    L.mvgd_row_signs.argtypes = [C.POINTER(Ell), _P, _P]
+    L.mvgd_row_signs.restype = C.c_int
     _lib = L
     return L
 

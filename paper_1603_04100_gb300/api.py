@@ -15,7 +15,7 @@ import torch
 
 from . import _lib as LB
 from ._lib import (DELTA_MEAN_NN, DELTA_QUARTER_RANGE, FP32_REFINE, FP64, SPMV_F32, SPMV_F64,  # noqa: F401
-                   SPMV_F64_HILO, MvgdError)
+                   SPMV_F64_HILO, ROW_LS, ROW_MVGD, MvgdError)
 
 SLICE = 32
 
@@ -115,8 +115,10 @@ def ell_alloc(n: int, k: int, prec: int, device) -> tuple:
 
 def assemble(pts: torch.Tensor, nbr: torch.Tensor, *, prec: int = FP64, order: torch.Tensor | None = None,
              delta_kind: int = DELTA_MEAN_NN, delta_m: int = 6, delta_scale: float = 1.0,
-             want_h: bool = True, want_status: bool = True, stream=None, out: Operator | None = None) -> Operator:
-    """MVGD rows (Sec. 2, Sec. 3.1) for every point into a sliced ELL operator."""
+             want_h: bool = True, want_status: bool = True, stream=None, out: Operator | None = None,
+             variant: int = LB.ROW_MVGD) -> Operator:
+    """MVGD rows (Sec. 2, Sec. 3.1) for every point into a sliced ELL operator; variant
+    ROW_LS forms the plain least-squares comparator rows instead."""
     _require_cuda(pts, torch.float64, "pts")
     _require_cuda(nbr, torch.int32, "nbr")
     n, k = nbr.shape
@@ -133,7 +135,8 @@ def assemble(pts: torch.Tensor, nbr: torch.Tensor, *, prec: int = FP64, order: t
         op = out
         op.order = order
     ws = _workspace(L.mvgd_assemble_workspace_bytes(n), pts.device) if order is not None else None
-    rule = LB.DeltaRule(delta_kind, delta_m if delta_kind == DELTA_MEAN_NN else 0, float(delta_scale))
+    rule = LB.DeltaRule(delta_kind, delta_m if delta_kind == DELTA_MEAN_NN else 0, float(delta_scale),
+                        int(variant))
     c = op.cstruct()
     LB.check("mvgd_assemble", L.mvgd_assemble(_vp(pts), n, k, _vp(nbr), rule, C.byref(c), _vp(op.h),
                                                _vp(op.status), _vp(op.bad_rows), _vp(ws),
@@ -156,6 +159,17 @@ def spmv(op: Operator, x: torch.Tensor, *, mode: int | None = None, sigma: float
     c = op.cstruct()
     LB.check("mvgd_spmv", L.mvgd_spmv(C.byref(c), mode, nrhs, sigma, alpha, _vp(x), beta, _vp(y), _stream(stream)))
     return y
+
+
+def row_signs(op: Operator, stream=None) -> dict:
+    """Sign pattern of the operator's rows (mvgd_row_signs): rows whose neighbour
+    weights are all >= 0 (the M-matrix pattern of sigma I - L), negative
+    neighbour weights, rows with a non-negative self weight."""
+    counts = torch.zeros(3, dtype=torch.int64, device=op.col.device)
+    c = op.cstruct()
+    LB.check("mvgd_row_signs", LB.load().mvgd_row_signs(C.byref(c), _vp(counts), _stream(stream)))
+    m_rows, neg, self_nonneg = (int(v) for v in counts.cpu().tolist())
+    return {"m_pattern_rows": m_rows, "negative_weights": neg, "nonneg_self_rows": self_nonneg, "rows": op.n}
 
 
 @dataclass

@@ -37,6 +37,7 @@ struct AsmArgs {
     const int32_t* inv;     // point -> stored row (only with order)
     int delta_kind, delta_m;
     double delta_scale;
+    int variant;  // mvgd_row_variant
     int prec;
     int32_t* col;
     void* val;
@@ -220,7 +221,9 @@ __device__ __forceinline__ void assemble_slice(const AsmArgs& A, int64_t slice) 
     const double g11 = (1.0 + zy * zy) * iW, g12 = -zx * zy * iW, g22 = (1.0 + zx * zx) * iW;
     const double Hs = g11 * zxx + 2.0 * g12 * zxy + g22 * zyy;
     const double A1 = -Hs * zx * iW, A2 = -Hs * zy * iW, A3 = g11, A4 = 2.0 * g12, A5 = g22;
-    const double c0 = 2.0 * (A3 + A5);
+    // the least-squares comparator drops the centre-value term: c~_0 = 0 and no
+    // self correction, which leaves the LB of the fitted quadratic itself
+    const double c0 = A.variant == MVGD_ROW_LS ? 0.0 : 2.0 * (A3 + A5);
     const double ct[6] = {c0, A1 * h, A2 * h, 2.0 * A3, A4, 2.0 * A5};
 
     // t = R^-T c~ (forward substitution), y = Q [t; 0]
@@ -339,6 +342,7 @@ MVGD_API mvgd_status mvgd_assemble(const double* pts, int64_t n, int32_t k, cons
     if (rule.kind != MVGD_DELTA_QUARTER_RANGE && rule.kind != MVGD_DELTA_MEAN_NN) return MVGD_EINVAL;
     if (rule.kind == MVGD_DELTA_MEAN_NN && (rule.m < 1 || rule.m > k)) return MVGD_EINVAL;
     if (!(rule.scale > 0)) return MVGD_EINVAL;
+    if (rule.variant != MVGD_ROW_MVGD && rule.variant != MVGD_ROW_LS) return MVGD_EINVAL;
     if (!aligned(pts) || !aligned(nbr) || !aligned(L->col) || !aligned(L->val) || !aligned(L->val_lo) ||
         !aligned(L->order) || !aligned(h) || !aligned(row_status) || !aligned(bad_rows) || !aligned(ws))
         return MVGD_EINVAL;
@@ -350,6 +354,7 @@ MVGD_API mvgd_status mvgd_assemble(const double* pts, int64_t n, int32_t k, cons
     A.delta_kind = rule.kind;
     A.delta_m = rule.kind == MVGD_DELTA_MEAN_NN ? rule.m : 0;
     A.delta_scale = rule.scale;
+    A.variant = rule.variant;
     A.prec = L->prec;
     A.col = L->col; A.val = L->val; A.val_lo = L->val_lo;
     A.h_out = h; A.status = row_status; A.bad_rows = bad_rows;
@@ -378,6 +383,7 @@ MVGD_API mvgd_status mvgd_assemble_batch(const mvgd_assemble_item* items, int32_
     if (!items || count < 1 || !ws || !aligned(ws) || !aligned(bad_rows)) return MVGD_EINVAL;
     if (rule.kind != MVGD_DELTA_QUARTER_RANGE && rule.kind != MVGD_DELTA_MEAN_NN) return MVGD_EINVAL;
     if (!(rule.scale > 0)) return MVGD_EINVAL;
+    if (rule.variant != MVGD_ROW_MVGD && rule.variant != MVGD_ROW_LS) return MVGD_EINVAL;
     size_t need = align_up(sizeof(AsmItem) * (size_t)count);
     int kmax = 0;
     for (int i = 0; i < count; i++) {
@@ -423,6 +429,7 @@ MVGD_API mvgd_status mvgd_assemble_batch(const mvgd_assemble_item* items, int32_
         a.a.delta_kind = rule.kind;
         a.a.delta_m = rule.kind == MVGD_DELTA_MEAN_NN ? rule.m : 0;
         a.a.delta_scale = rule.scale;
+        a.a.variant = rule.variant;
         a.a.prec = L.prec;
         a.a.col = L.col;
         a.a.val = L.val;
@@ -442,5 +449,57 @@ MVGD_API mvgd_status mvgd_assemble_batch(const mvgd_assemble_item* items, int32_
     MVGD_CUDA_TRY(cudaFuncSetAttribute(k_assemble_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (slices >= (1ll << 31)) return MVGD_EINVAL;
     k_assemble_batch<<<(unsigned)slices, kWarp, smem, s>>>(table, count);
+    return launch_status();
+}
+
+// ---------------------------------------------------------------------------
+// Sign pattern of the assembled rows (Sec. 3.2, Sec. 4.1): the rows sum to
+// zero, so a row whose neighbour weights are all >= 0 gives sigma I - L a
+// diagonally dominant row with non-positive off-diagonal entries (the
+// M-matrix pattern).  Integer counts, summed with atomics: exact.
+// ---------------------------------------------------------------------------
+namespace mvgd {
+namespace {
+
+__global__ void k_row_signs(mvgd_ell L, unsigned long long* counts) {
+    const int k = L.k, m = k + 1;
+    unsigned long long pattern = 0, negative = 0, self_nonneg = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
+        auto weight = [&](int s) {
+            const int64_t e = vb + (int64_t)s * kSlice;
+            return L.prec == MVGD_FP64 ? static_cast<const double*>(L.val)[e]
+                                       : (double)static_cast<const float*>(L.val)[e] + (double)L.val_lo[e];
+        };
+        int neg = 0;
+        for (int s = 1; s < m; s++) neg += weight(s) < 0.0 ? 1 : 0;
+        pattern += neg == 0 ? 1 : 0;
+        negative += (unsigned long long)neg;
+        self_nonneg += weight(0) >= 0.0 ? 1 : 0;
+    }
+    pattern = warp_sum(pattern);
+    negative = warp_sum(negative);
+    self_nonneg = warp_sum(self_nonneg);
+    if (lane_id() == 0) {
+        atomicAdd(&counts[0], pattern);
+        atomicAdd(&counts[1], negative);
+        atomicAdd(&counts[2], self_nonneg);
+    }
+}
+
+}  // namespace
+}  // namespace mvgd
+
+MVGD_API mvgd_status mvgd_row_signs(const mvgd_ell* L, int64_t* counts, mvgd_stream_t stream) {
+    if (!L || !counts || !L->val || L->n < 1 || L->k < kMinK || L->k > kMaxK) return MVGD_EINVAL;
+    if (L->prec != MVGD_FP64 && L->prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    if (L->prec == MVGD_FP32_REFINE && !L->val_lo) return MVGD_EINVAL;
+    if (!aligned(L->val) || !aligned(L->val_lo) || (reinterpret_cast<uintptr_t>(counts) & 7) != 0)
+        return MVGD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MVGD_CUDA_TRY(cudaMemsetAsync(counts, 0, 3 * sizeof(int64_t), s));
+    const int64_t blocks = (L->n + 255) / 256;
+    k_row_signs<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(
+        *L, reinterpret_cast<unsigned long long*>(counts));
     return launch_status();
 }

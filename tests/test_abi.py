@@ -82,6 +82,13 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
     bad = LB.DeltaRule(LB.DELTA_MEAN_NN, 11, 1.0)
     assert L.mvgd_assemble(C.c_void_p(256), 100, 10, C.c_void_p(512), bad, C.byref(e), None, None, None, None, 0,
                            None) == LB.EINVAL                 # m > k
+    bad = LB.DeltaRule(LB.DELTA_MEAN_NN, 6, 1.0, 2)
+    assert L.mvgd_assemble(C.c_void_p(256), 100, 10, C.c_void_p(512), bad, C.byref(e), None, None, None, None, 0,
+                           None) == LB.EINVAL                 # unknown row variant
+    assert L.mvgd_row_signs(None, C.c_void_p(256), None) == LB.EINVAL
+    assert L.mvgd_row_signs(C.byref(e), C.c_void_p(260), None) == LB.EINVAL  # counts not 8-byte aligned
+    e4 = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
+    assert L.mvgd_row_signs(C.byref(e4), C.c_void_p(256), None) == LB.EINVAL  # k < 5
     assert L.mvgd_spmv(C.byref(e), LB.SPMV_F32, 1, 1.0, 1.0, C.c_void_p(256), 0.0, C.c_void_p(512),
                        None) == LB.EINVAL                     # FP32 mode on an FP64 operator
     opts = LB.SolveOpts(0.0, 10, 10, 1e-5, 5, 0)
@@ -99,3 +106,10 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
     amg_opts = LB.SolveOpts(1e-8, 10, 10, 1e-5, 5, 2, C.c_void_p(0))
     assert L.mvgd_request_init(C.c_void_p(1024), 1 << 30, C.byref(e), 1, 1.0, C.c_void_p(256), None,
                                C.byref(amg_opts), None) == LB.EINVAL  # precond 2 needs a hierarchy
+
+
+def test_binding_modules_import():
+    # the Python layer imports without a GPU (the CUDA path is only reached on a call)
+    import importlib
+    for mod in ("api", "batch", "pipeline", "serve", "inputs", "profile_case"):
+        importlib.import_module(f"paper_1603_04100_gb300.{mod}")

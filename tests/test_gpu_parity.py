@@ -123,6 +123,56 @@ def test_assemble_mixed_hilo(dev, k):
     assert err.max() <= W_TOL, err.max()
 
 
+@pytest.mark.parametrize("name", ["fib2562", "rand20001", "torus12345"])
+@pytest.mark.parametrize("k", [12, 20])
+def test_assemble_least_squares_rows(dev, name, k):
+    # the comparator of Sec. 2 (mvgd_delta_rule.variant = ROW_LS) against the
+    # oracle's own least-squares rows, same bound as the MVGD rows
+    api = _api()
+    p = CLOUDS[name]()
+    pt = torch.from_numpy(p).to(dev)
+    nbr_t = api.knn(pt, k)
+    nbr = nbr_t.cpu().numpy()
+    op = api.assemble(pt, nbr_t, prec=api.FP64, variant=api.ROW_LS)
+    val, st, _, _ = oracle.assemble(p, nbr, variant=oracle.VARIANT_LS)
+    err = row_relerr(op.weights(), val)
+    assert err.max() <= W_TOL, (err.max(), int(err.argmax()))
+    assert np.all(np.abs(val.sum(1)) <= 1e-9 * np.abs(val).sum(1))  # consistent: rows sum to zero
+
+
+def _sign_counts_agree(got, val):
+    """GPU counts against the oracle's on its own rows; a neighbour weight within
+    1e-9 of zero (relative to its row) may take either sign, so each such row may move a count by one."""
+    want = oracle.row_sign_counts(val)
+    scale = np.abs(val).max(1, keepdims=True)
+    loose = int(np.count_nonzero(np.any(np.abs(val) <= 1e-9 * scale, axis=1)))
+    diffs = [abs(got["m_pattern_rows"] - want[0]), abs(got["negative_weights"] - want[1]),
+             abs(got["nonneg_self_rows"] - want[2])]
+    assert max(diffs) <= loose, (got, want, loose)
+    return want
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32_REFINE"])
+def test_row_signs_match_oracle(dev, prec_name):
+    # Sec. 3.2 / Sec. 4.1: the share of rows with the M-matrix sign pattern, MVGD
+    # against the least-squares comparator, counted on the GPU and by the oracle
+    api = _api()
+    prec = getattr(api, prec_name)
+    p = CLOUDS["fib2562"]()
+    pt = torch.from_numpy(p).to(dev)
+    nbr_t = api.knn(pt, 12)
+    nbr = nbr_t.cpu().numpy()
+    out = {}
+    for variant, ovar in ((api.ROW_MVGD, oracle.VARIANT_MVGD), (api.ROW_LS, oracle.VARIANT_LS)):
+        op = api.assemble(pt, nbr_t, prec=prec, variant=variant)
+        got = api.row_signs(op)
+        assert got["rows"] == len(p)
+        val, _, _, _ = oracle.assemble(p, nbr, variant=ovar)
+        out[variant] = _sign_counts_agree(got, val)
+    # the MVGD rows keep the pattern far more often than the plain least-squares rows
+    assert out[api.ROW_MVGD][0] > out[api.ROW_LS][0]
+
+
 def test_assemble_with_locality_order(dev):
     api = _api()
     p = I.random_sphere(20001, 7)

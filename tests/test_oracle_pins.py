@@ -145,6 +145,26 @@ def test_knn_grid_equals_brute(maker):
         np.testing.assert_array_equal(oracle.knn_grid(p, k), oracle.knn_brute(p, k))
 
 
+def test_row_sign_counts_on_the_line_example():
+    # the 1-D rows of Sec. 3.2 laid out as [self, neighbours]: the MVGD row has the
+    # M-matrix sign pattern exactly for 3/5 <= r <= 24/5 (Eq. 8), the least-squares
+    # row (2, -1, -2, -1, 2) never (two negative neighbour weights)
+    xs = np.arange(-2, 3, dtype=np.float64)
+    rs = [0.3, 0.6, 1.0, 2.0, 4.8, 6.0]
+    rows = []
+    for r in rs:
+        w = oracle.line_weights(xs, 2, h=math.sqrt(r), variant=oracle.VARIANT_MVGD)
+        w[np.abs(w) <= 1e-12 * np.abs(w).max()] = 0.0  # the interval's ends hold exact zeros
+        rows.append(np.concatenate([[w[2]], np.delete(w, 2)]))
+    m_rows, neg, self_nonneg = oracle.row_sign_counts(np.array(rows))
+    assert m_rows == sum(1 for r in rs if 0.6 <= r <= 4.8) == 4
+    assert self_nonneg == 0
+    ls = oracle.line_weights(xs, 2, h=1.0, variant=oracle.VARIANT_LS)
+    assert oracle.row_sign_counts(np.array([np.concatenate([[ls[2]], np.delete(ls, 2)])])) == (0, 2, 0)
+    # by hand: one row of each kind
+    assert oracle.row_sign_counts(np.array([[-3.0, 1, 2, 0], [-1.0, 2, -1, 0], [0.5, -1, 0.5, 0]])) == (1, 2, 1)
+
+
 # ---------------------------------------------------------------------------
 # Structural invariants of the MVGD rows
 # ---------------------------------------------------------------------------
