@@ -37,6 +37,11 @@ sys.path.insert(0, str(ROOT))
 METRIC = "MVGD points/s (assembly+solve to 1e-8 rel) batched/served vs plain; p50/p99 ms"
 N_DEFAULT, K_DEFAULT, SEED = 1_048_576, 20, 0
 RTOL = 1e-8
+# DRAM bytes (read + write) per iteration of k_solve<1,1,1> on the bench workload
+# (N = 1,048,576, K = 20, multigrid, FP32 inner): an ncu capture of a 20-iteration
+# launch of the current kernel read 21.51 GB and wrote 0.65 GB.  Valid for this
+# kernel and workload only; any other path or size reports traffic null.
+KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = (21.515e9 + 0.646e9) / 20
 BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see run_batched)
 WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
             "6 nearest, u = 5z^3-3z, f = 13u, (I-L)u = f to 1e-8 relative residual")
@@ -523,7 +528,10 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = bytes_solve / (solve_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": (KSOLVE_MIXED_AMG_DRAM_PER_ITERATION * info[0]
+                            if best == "fp32_refine+amg" and n == N_DEFAULT and k == K_DEFAULT else None),
+                "traffic_note": "ncu DRAM bytes per iteration of the same kernel on this workload x the launch's "
+                                "iterations; below the algorithmic bytes because the Krylov vectors stay in L2",
                 "kernel": "k_solve (persistent BiCGSTAB, " + ("FP32 inner + FP64 refinement" if mixed_best else "FP64")
                           + (", multigrid V-cycle preconditioner)" if R["amg"] else ", row scaling)"),
                 "peak_kind": f"hbm_gbs of {peak_kind}", "bytes_per_launch": bytes_solve, "launch_ms": solve_ms,
