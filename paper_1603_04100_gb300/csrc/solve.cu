@@ -729,12 +729,25 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
         double acc[kChan * QT];
 #pragma unroll
         for (int e = 0; e < kChan * QT; e++) acc[e] = 0.0;
-        for (int l = tid; l < P.nchunk; l += kThreads)
+        if (P.Q == 1 && (P.nchunk & 1) == 0) {
+            // one right-hand side: two consecutive tiles' partials per (16-byte) load,
+            // half the dependent L2 round trips of the general loop below
+            for (int l = 2 * tid; l < P.nchunk; l += 2 * kThreads)
 #pragma unroll
-            for (int e = 0; e < kChan * QT; e++) {
-                const int ch = e / QT, q = e % QT;
-                if (q < P.Q) acc[e] += __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q]);
-            }
+                for (int ch = 0; ch < kChan; ch++) {
+                    const double2 v =
+                        __ldcg(reinterpret_cast<const double2*>(&P.part[((int64_t)slot * kChan + ch) * P.nchunk + l]));
+                    acc[ch * QT] += v.x;
+                    acc[ch * QT] += v.y;
+                }
+        } else {
+            for (int l = tid; l < P.nchunk; l += kThreads)
+#pragma unroll
+                for (int e = 0; e < kChan * QT; e++) {
+                    const int ch = e / QT, q = e % QT;
+                    if (q < P.Q) acc[e] += __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q]);
+                }
+        }
 #pragma unroll
         for (int e = 0; e < kChan * QT; e++) {
             const double v = warp_sum(acc[e]);
