@@ -195,6 +195,20 @@ mvgd_status mvgd_assemble_batch(const mvgd_assemble_item *items, int32_t count, 
  * Asynchronous; MVGD_EINVAL on a null pointer or out-of-range sizes. */
 mvgd_status mvgd_row_signs(const mvgd_ell *L, int64_t *counts, mvgd_stream_t stream);
 
+/* Dirichlet boundary rows for point clouds of open surfaces (Sec. 3.1): the
+ * condition U = g is enforced at the boundary points and the MVGD row kept at
+ * every interior point, whose neighbours may include boundary points.  Zeroes
+ * every weight (self included) of the rows of the points flagged in boundary,
+ * so that row of sigma I - L becomes sigma e_r; the caller puts sigma g_i
+ * into f at those points.
+ *   boundary: DEVICE uint8 [n] in point order (nonzero = boundary point);
+ *             stored row r is point L->order[r] (or r without an order).
+ *   count:    optional DEVICE int32, overwritten with the number of rows zeroed
+ *             (4-byte aligned).
+ * Call after mvgd_assemble and before mvgd_amg_setup / mvgd_solve.
+ * Asynchronous; MVGD_EINVAL on a null operator or mask, or out-of-range sizes. */
+mvgd_status mvgd_dirichlet_rows(mvgd_ell *L, const uint8_t *boundary, int32_t *count, mvgd_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Operator application (the product every Krylov step repeats, Sec. 3.1 and
  * Sec. 4.2):  y = alpha * (sigma x - L x) + beta * y  for nrhs right-hand

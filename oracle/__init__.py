@@ -16,6 +16,7 @@ the paper they follow):
   solvers of (sigma I - L) u = f.
 * ``line_weights``: the 1-D worked example of Sec. 3.2.
 * ``row_sign_counts``: the M-matrix sign pattern of rows (Sec. 3.2, Sec. 4.1).
+* ``dirichlet_rows``: boundary rows of open surfaces (Sec. 3.1).
 * ``normal_matrix``: the 6x6 normal-equation matrix of Sec. 2 as printed.
 """
 from __future__ import annotations
@@ -176,6 +177,15 @@ def row_sign_counts(val) -> tuple:
     nbrs = val[:, 1:]
     return (int(np.count_nonzero(np.all(nbrs >= 0.0, axis=1))), int(np.count_nonzero(nbrs < 0.0)),
             int(np.count_nonzero(val[:, 0] >= 0.0)))
+
+
+def dirichlet_rows(val, boundary) -> np.ndarray:
+    """Open surfaces with U = g on the boundary (Sec. 3.1): the rows [n][k+1] of the
+    boundary points become zero, so those rows of sigma I - L read sigma u_i = f_i,
+    and every interior row keeps its MVGD weights."""
+    out = np.array(val, dtype=np.float64, copy=True)
+    out[np.asarray(boundary).astype(bool)] = 0.0
+    return out
 
 
 def normal_matrix(x, y) -> np.ndarray:

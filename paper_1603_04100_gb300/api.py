@@ -172,6 +172,18 @@ def row_signs(op: Operator, stream=None) -> dict:
     return {"m_pattern_rows": m_rows, "negative_weights": neg, "nonneg_self_rows": self_nonneg, "rows": op.n}
 
 
+def dirichlet_rows(op: Operator, boundary: torch.Tensor, stream=None) -> int:
+    """Dirichlet rows (mvgd_dirichlet_rows): zero the rows of the points flagged in
+    boundary (uint8 [n], point order), so those rows of sigma I - L read sigma u_i = f_i.
+    Returns the number of rows zeroed."""
+    _require_cuda(boundary, torch.uint8, "boundary")
+    count = torch.zeros(1, dtype=torch.int32, device=op.col.device)
+    c = op.cstruct()
+    LB.check("mvgd_dirichlet_rows", LB.load().mvgd_dirichlet_rows(C.byref(c), _vp(boundary), _vp(count),
+                                                                   _stream(stream)))
+    return int(count.item())
+
+
 @dataclass
 class SolveResult:
     u: torch.Tensor

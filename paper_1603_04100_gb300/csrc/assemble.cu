@@ -503,3 +503,50 @@ MVGD_API mvgd_status mvgd_row_signs(const mvgd_ell* L, int64_t* counts, mvgd_str
         *L, reinterpret_cast<unsigned long long*>(counts));
     return launch_status();
 }
+
+// ---------------------------------------------------------------------------
+// Dirichlet boundary rows (open surfaces, Sec. 3.1): U = g is enforced at the
+// boundary points and the MVGD row kept at the interior points.
+// ---------------------------------------------------------------------------
+namespace mvgd {
+namespace {
+
+__global__ void k_dirichlet_rows(mvgd_ell L, const uint8_t* __restrict__ boundary, int32_t* count) {
+    const int m = L.k + 1;
+    int mine = 0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = L.order ? (int64_t)L.order[r] : r;
+        if (!boundary[p]) continue;
+        const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
+        for (int s = 0; s < m; s++) {
+            const int64_t e = vb + (int64_t)s * kSlice;
+            if (L.prec == MVGD_FP64) {
+                static_cast<double*>(L.val)[e] = 0.0;
+            } else {
+                static_cast<float*>(L.val)[e] = 0.0f;
+                L.val_lo[e] = 0.0f;
+            }
+        }
+        mine++;
+    }
+    mine = warp_sum(mine);
+    if (count && lane_id() == 0 && mine) atomicAdd(count, mine);
+}
+
+}  // namespace
+}  // namespace mvgd
+
+MVGD_API mvgd_status mvgd_dirichlet_rows(mvgd_ell* L, const uint8_t* boundary, int32_t* count,
+                                         mvgd_stream_t stream) {
+    if (!L || !boundary || !L->val || L->n < 1 || L->n >= (1ll << 31) || L->k < kMinK || L->k > kMaxK)
+        return MVGD_EINVAL;
+    if (L->prec != MVGD_FP64 && L->prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    if (L->prec == MVGD_FP32_REFINE && !L->val_lo) return MVGD_EINVAL;
+    if (!aligned(L->val) || !aligned(L->val_lo) || (reinterpret_cast<uintptr_t>(count) & 3) != 0)
+        return MVGD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (count) MVGD_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), s));
+    const int64_t blocks = (L->n + 255) / 256;
+    k_dirichlet_rows<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(*L, boundary, count);
+    return launch_status();
+}

@@ -61,6 +61,23 @@ def random_sphere(n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(g / np.linalg.norm(g, axis=1, keepdims=True))
 
 
+def hemisphere(n: int, seed: int, rim: float = 2.0) -> tuple[np.ndarray, np.ndarray]:
+    """n uniform random points of the open upper unit hemisphere (z > 0) and a
+    boundary mask: the points within rim * sqrt(2 pi / n) of the rim z = 0, a band
+    about `rim` point spacings deep (uint8 [n], 1 = boundary)."""
+    rng = _rng(seed)
+    out, have = [], 0
+    while have < n:
+        g = rng.standard_normal((2 * (n - have) + 64, 3))
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        g = g[g[:, 2] > 0.0]
+        out.append(g)
+        have += g.shape[0]
+    pts = np.ascontiguousarray(np.concatenate(out)[:n])
+    boundary = (pts[:, 2] < rim * math.sqrt(2.0 * math.pi / n)).astype(np.uint8)
+    return pts, boundary
+
+
 def morton_sorted(pts: np.ndarray, bits: int = 10) -> np.ndarray:
     """The same points reordered along a Z-order curve of their bounding cube
     (`bits` per axis, stable in the original index): consecutive points are

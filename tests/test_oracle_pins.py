@@ -366,3 +366,28 @@ def test_solvers_match_direct(solver):
         u, it, rr, st = oracle.gmres(val, nb, pr.f[:, 0], rtol=1e-13, restart=60)
     assert st == 0 and rr <= 1e-13
     assert np.linalg.norm(u - want) <= 1e-10 * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------------------
+# Open surfaces: Dirichlet rows (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+def test_dirichlet_hemisphere_converges_at_second_order():
+    # u = z on the upper hemisphere: Delta_S z = -2z, so (I - L) u = 3z inside and
+    # u = z is enforced on the rim band; the error against z falls like h^2
+    errs = []
+    for n in (4000, 16000):
+        p, b = I.hemisphere(n, 3)
+        nbr = oracle.knn_grid(p, 20)
+        val, st, _, _ = oracle.assemble(p, nbr)
+        assert int(st.max()) == 0
+        v = oracle.dirichlet_rows(val, b)
+        assert np.all(v[b == 1] == 0.0) and np.array_equal(v[b == 0], val[b == 0])
+        z = p[:, 2]
+        f = np.where(b == 1, z, 3.0 * z)
+        u, _, rel, s = oracle.bicgstab(v, nbr, f, 1.0, rtol=1e-12, maxit=20000)
+        assert s == 0 and rel <= 1e-12
+        # the boundary rows read u_i = g_i, to the solver's tolerance
+        assert np.abs(u[b == 1] - z[b == 1]).max() <= 1e-10
+        errs.append(np.abs(u - z).max())
+    assert errs[1] < 1e-4 and errs[0] / errs[1] > 3.0, errs  # observed order in h above 1.58
