@@ -210,6 +210,24 @@ mvgd_status mvgd_row_signs(const mvgd_ell *L, int64_t *counts, mvgd_stream_t str
 mvgd_status mvgd_dirichlet_rows(mvgd_ell *L, const uint8_t *boundary, int32_t *count, mvgd_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Sets of vectors, for the subspace iteration behind the lowest eigenpairs of
+ * the LB operator (Sec. 4.3).  A set of p vectors of length n (FP64, DEVICE,
+ * 256-byte aligned) is stored in blocks of w interleaved columns (1 <= w <= 8),
+ * each block a right-hand-side array [n][w] of mvgd_solve / mvgd_spmv:
+ *   element (r, c) at (c / w) * n * w + r * w + (c % w);  p, q multiples of w, <= 64.
+ * mvgd_block_gram: G = X^T Y (p x q, row-major, DEVICE) summed in a fixed
+ *   order (256 row ranges, each in row order, then the ranges in order), so the
+ *   result does not depend on the GPU; ws sized by mvgd_block_gram_workspace_bytes.
+ * mvgd_block_combine: Y = X C with C p x q row-major (DEVICE); X and Y distinct.
+ * Both asynchronous; MVGD_EINVAL on bad shapes or pointers.
+ * ------------------------------------------------------------------------ */
+size_t mvgd_block_gram_workspace_bytes(int32_t p, int32_t q);
+mvgd_status mvgd_block_gram(const double *X, int32_t p, const double *Y, int32_t q, int64_t n, int32_t w,
+                            double *G, void *ws, size_t ws_bytes, mvgd_stream_t stream);
+mvgd_status mvgd_block_combine(const double *X, int32_t p, const double *C, int32_t q, int64_t n, int32_t w,
+                               double *Y, mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Operator application (the product every Krylov step repeats, Sec. 3.1 and
  * Sec. 4.2):  y = alpha * (sigma x - L x) + beta * y  for nrhs right-hand
  * sides stored interleaved, x and y [n][nrhs] in STORED row order.

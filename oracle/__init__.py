@@ -17,6 +17,8 @@ the paper they follow):
 * ``line_weights``: the 1-D worked example of Sec. 3.2.
 * ``row_sign_counts``: the M-matrix sign pattern of rows (Sec. 3.2, Sec. 4.1).
 * ``dirichlet_rows``: boundary rows of open surfaces (Sec. 3.1).
+* ``lb_eigenvalues``, ``multiplet_errors``: the lowest LB eigenvalues and the
+  error measures of Sec. 4.3.
 * ``normal_matrix``: the 6x6 normal-equation matrix of Sec. 2 as printed.
 """
 from __future__ import annotations
@@ -186,6 +188,26 @@ def dirichlet_rows(val, boundary) -> np.ndarray:
     out = np.array(val, dtype=np.float64, copy=True)
     out[np.asarray(boundary).astype(bool)] = 0.0
     return out
+
+
+def lb_eigenvalues(val, nbr, nev: int, shift: float = 0.5) -> np.ndarray:
+    """The nev smallest eigenvalues lambda of -L (Sec. 4.3), as the paper takes them:
+    a sparse eigensolver on the assembled matrix (ARPACK in shift-invert mode about
+    lambda = -shift).  Real parts, ascending; the matrix is not symmetric, so a
+    multiplet can carry small imaginary parts."""
+    import scipy.sparse.linalg as spl
+    Lm = to_csr(val, nbr).tocsc()
+    w = spl.eigs(Lm, k=nev, sigma=shift, which="LM", return_eigenvectors=False)
+    return np.sort(-w.real)
+
+
+def multiplet_errors(lams, n: int) -> tuple:
+    """E^2_n and E^inf_n of Sec. 4.3 for the sphere's n-th eigenvalue n (n + 1),
+    multiplicity 2n + 1: relative errors of the eigenvalues n^2 .. n^2 + 2n of the
+    ascending list lams (RMS and maximum)."""
+    lam = n * (n + 1.0)
+    r = (np.asarray(lams, dtype=np.float64)[n * n:n * n + 2 * n + 1] - lam) / lam
+    return float(np.sqrt(np.mean(r * r))), float(np.abs(r).max())
 
 
 def normal_matrix(x, y) -> np.ndarray:

@@ -27,7 +27,8 @@ EXPORTS = (
     "mvgd_request_finish", "mvgd_assemble_batch_workspace_bytes", "mvgd_assemble_batch", "mvgd_request_poll",
     "mvgd_knn_noalloc", "mvgd_amg_workspace_bytes", "mvgd_amg_setup", "mvgd_amg_describe",
     "mvgd_amg_apply_workspace_bytes", "mvgd_amg_apply", "mvgd_trace_enable", "mvgd_trace_read",
-    "mvgd_row_signs", "mvgd_dirichlet_rows",
+    "mvgd_row_signs", "mvgd_dirichlet_rows", "mvgd_block_gram_workspace_bytes", "mvgd_block_gram",
+    "mvgd_block_combine",
 )
 PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
 AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
@@ -148,6 +149,12 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_row_signs.restype = C.c_int
     L.mvgd_dirichlet_rows.argtypes = [C.POINTER(Ell), _P, _P, _P]
     L.mvgd_dirichlet_rows.restype = C.c_int
+    L.mvgd_block_gram_workspace_bytes.argtypes = [C.c_int32, C.c_int32]
+    L.mvgd_block_gram_workspace_bytes.restype = C.c_size_t
+    L.mvgd_block_gram.argtypes = [_P, C.c_int32, _P, C.c_int32, C.c_int64, C.c_int32, _P, _P, C.c_size_t, _P]
+    L.mvgd_block_gram.restype = C.c_int
+    L.mvgd_block_combine.argtypes = [_P, C.c_int32, _P, C.c_int32, C.c_int64, C.c_int32, _P, _P]
+    L.mvgd_block_combine.restype = C.c_int
     _lib = L
     return L
 

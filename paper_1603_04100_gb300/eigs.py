@@ -1,0 +1,132 @@
+"""Lowest eigenpairs of the discrete LB operator (Sec. 4.3: -Delta_S v = lambda v).
+
+Shift-invert subspace iteration on A = sigma I - L, whose smallest eigenvalues
+1 + lambda belong to the smallest lambda:
+  Y = A^-1 X           p/8 calls of mvgd_solve, 8 right-hand sides each, with the
+                       multigrid preconditioner built once (mvgd_amg_setup);
+  X = orthonormal(Y)   Cholesky QR twice: G = Y^T Y (mvgd_block_gram),
+                       X = Y R^-1 (mvgd_block_combine);
+  H = X^T (L X)        mvgd_spmv with sigma = 0, alpha = -1 per block, then a Gram;
+and the Ritz values of the p x p matrix H estimate the eigenvalues of L
+(lambda = -theta).  Every O(n) step runs in the library's kernels; only the
+p x p Cholesky factor and the Ritz values of H (p <= 64) are computed on the
+host, as in reverse-communication eigensolvers.  The operator is not
+symmetric, so H is not either; its eigenvalues near a multiplet of the
+sphere come out real up to rounding, and their real parts are reported.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as LB
+from . import api
+
+W = 8  # columns per block: the solver's right-hand-side limit
+
+
+@dataclass
+class EigResult:
+    values: np.ndarray      # the nev smallest lambda, ascending
+    vectors: torch.Tensor   # [p/8][n][8] orthonormal basis of the converged subspace (stored order)
+    iterations: int
+    change: float           # largest relative change of the nev values in the last iteration
+    solves: int             # mvgd_solve calls made
+
+
+def _blocks(n: int, p: int, device) -> torch.Tensor:
+    return torch.empty((p // W, n, W), dtype=torch.float64, device=device)
+
+
+class _Kit:
+    """Gram and combination calls on block-major [p/8][n][8] sets."""
+
+    def __init__(self, n: int, p: int, device, stream):
+        self.L = LB.load()
+        self.n, self.p, self.dev = n, p, device
+        self.s = api._stream(stream)
+        self.ws = torch.empty(self.L.mvgd_block_gram_workspace_bytes(p, p), dtype=torch.uint8, device=device)
+        self.G = torch.empty((p, p), dtype=torch.float64, device=device)
+        self.Cm = torch.empty((p, p), dtype=torch.float64, device=device)
+
+    def gram(self, X: torch.Tensor, Y: torch.Tensor) -> np.ndarray:
+        LB.check("mvgd_block_gram", self.L.mvgd_block_gram(api._vp(X), self.p, api._vp(Y), self.p, self.n, W,
+                                                            api._vp(self.G), api._vp(self.ws), self.ws.numel(),
+                                                            self.s))
+        return self.G.cpu().numpy()
+
+    def combine(self, X: torch.Tensor, Cm: np.ndarray, Y: torch.Tensor) -> None:
+        self.Cm.copy_(torch.from_numpy(np.ascontiguousarray(Cm)))
+        LB.check("mvgd_block_combine", self.L.mvgd_block_combine(api._vp(X), self.p, api._vp(self.Cm), self.p,
+                                                                  self.n, W, api._vp(Y), self.s))
+
+    def orthonormalize(self, Y: torch.Tensor, X: torch.Tensor) -> None:
+        """X = Y R^-1 with R^T R = Y^T Y, twice (the second pass restores orthogonality)."""
+        src = Y
+        for _ in range(2):
+            G = self.gram(src, src)
+            G = 0.5 * (G + G.T)
+            R = np.linalg.cholesky(G).T
+            Rinv = np.linalg.solve(R, np.eye(self.p))
+            dst = X if src is Y else Y
+            self.combine(src, Rinv, dst)
+            src = dst
+        if src is not X:
+            X.copy_(src)
+
+
+def lowest_eigenpairs(op: api.Operator, nev: int, *, extra: int = 8, sigma: float = 1.0, tol: float = 1e-8,
+                      maxit: int = 200, rtol_solve: float = 1e-10, seed: int = 0, stream=None) -> EigResult:
+    """The nev smallest eigenvalues lambda of -L (op assembled in stored order)."""
+    p = ((nev + extra + W - 1) // W) * W
+    if p > 64:
+        raise ValueError("nev + extra must be at most 64")
+    dev = op.col.device
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    with torch.cuda.stream(st):  # torch's copies and the library's calls on one stream
+        return _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed)
+
+
+def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed) -> EigResult:
+    n, dev = op.n, op.col.device
+    # every vector stays in stored row order: the products read it so, and the
+    # solves are told there is no point order to map from
+    op = dataclasses.replace(op, order=None)
+    kit = _Kit(n, p, dev, st)
+    L = LB.load()
+    H_amg = api.amg_setup(op, sigma, stream=st)
+    X = _blocks(n, p, dev)
+    Y = _blocks(n, p, dev)
+    Z = _blocks(n, p, dev)
+    X.copy_(torch.from_numpy(np.random.default_rng(seed).standard_normal((p // W, n, W))))
+    kit.orthonormalize(X.clone(), X)
+    prev = None
+    change = np.inf
+    solves = 0
+    it = 0
+    for it in range(1, maxit + 1):
+        for b in range(p // W):  # Y = (sigma I - L)^-1 X
+            res = api.solve(op, X[b], rtol=rtol_solve, amg=H_amg, stream=st)
+            if any(s != LB.OK for s in res.status):
+                raise LB.MvgdError("mvgd_solve (shift-invert)", max(res.status))
+            Y[b].copy_(res.u)
+            solves += 1
+        kit.orthonormalize(Y, X)
+        mode = LB.SPMV_F64 if op.prec == LB.FP64 else LB.SPMV_F64_HILO  # FP64 (or hi + lo) weights
+        for b in range(p // W):  # Z = L X
+            c = op.cstruct()
+            LB.check("mvgd_spmv", L.mvgd_spmv(C.byref(c), mode, W, 0.0, -1.0, api._vp(X[b]), 0.0,
+                                                api._vp(Z[b]), api._stream(st)))
+        Hm = kit.gram(X, Z)
+        theta = np.linalg.eigvals(Hm)
+        lam = np.sort(-theta.real)[:nev]
+        if prev is not None:
+            change = float(np.max(np.abs(lam - prev) / np.maximum(np.abs(lam), 1.0)))
+            if change <= tol:
+                break
+        prev = lam
+    return EigResult(values=lam, vectors=X, iterations=it, change=change, solves=solves)
