@@ -226,6 +226,10 @@ mvgd_status mvgd_block_gram(const double *X, int32_t p, const double *Y, int32_t
                             double *G, void *ws, size_t ws_bytes, mvgd_stream_t stream);
 mvgd_status mvgd_block_combine(const double *X, int32_t p, const double *C, int32_t q, int64_t n, int32_t w,
                                double *Y, mvgd_stream_t stream);
+/* mvgd_block_zero_rows: X(r, c) = 0 for all c at the rows r with mask[r] != 0
+ * (DEVICE uint8 [n], the set's row order); keeps a subspace off Dirichlet rows. */
+mvgd_status mvgd_block_zero_rows(double *X, int32_t p, int64_t n, int32_t w, const uint8_t *mask,
+                                 mvgd_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Operator application (the product every Krylov step repeats, Sec. 3.1 and

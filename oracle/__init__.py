@@ -190,13 +190,18 @@ def dirichlet_rows(val, boundary) -> np.ndarray:
     return out
 
 
-def lb_eigenvalues(val, nbr, nev: int, shift: float = 0.5) -> np.ndarray:
+def lb_eigenvalues(val, nbr, nev: int, shift: float = 0.5, boundary=None) -> np.ndarray:
     """The nev smallest eigenvalues lambda of -L (Sec. 4.3), as the paper takes them:
     a sparse eigensolver on the assembled matrix (ARPACK in shift-invert mode about
     lambda = -shift).  Real parts, ascending; the matrix is not symmetric, so a
-    multiplet can carry small imaginary parts."""
+    multiplet can carry small imaginary parts.  With a boundary mask: the Dirichlet
+    problem, L restricted to the interior rows and columns."""
     import scipy.sparse.linalg as spl
-    Lm = to_csr(val, nbr).tocsc()
+    Lm = to_csr(val, nbr).tocsr()
+    if boundary is not None:
+        inner = np.flatnonzero(np.asarray(boundary) == 0)
+        Lm = Lm[inner][:, inner]
+    Lm = Lm.tocsc()
     w = spl.eigs(Lm, k=nev, sigma=shift, which="LM", return_eigenvectors=False)
     return np.sort(-w.real)
 

@@ -82,6 +82,14 @@ __global__ void __launch_bounds__(256) k_block_combine(const double* __restrict_
     }
 }
 
+// X(r, c) = 0 for every column c of the rows r flagged in mask
+__global__ void k_block_zero_rows(double* __restrict__ X, int p, int64_t n, int w, const uint8_t* __restrict__ mask) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * p; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / p;
+        if (mask[r]) X[at(r, (int)(e % p), n, w)] = 0.0;
+    }
+}
+
 bool bad_shape(int64_t n, int p, int q, int w) {
     return n < 1 || w < 1 || w > 8 || p < 1 || q < 1 || p > kMaxCols || q > kMaxCols || p % w != 0 || q % w != 0;
 }
@@ -115,5 +123,13 @@ MVGD_API mvgd_status mvgd_block_combine(const double* X, int32_t p, const double
     const int64_t blocks = (n * q + 255) / 256;
     k_block_combine<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, (cudaStream_t)stream>>>(X, p, C, q, n, w,
                                                                                                   Y);
+    return launch_status();
+}
+
+MVGD_API mvgd_status mvgd_block_zero_rows(double* X, int32_t p, int64_t n, int32_t w, const uint8_t* mask,
+                                          mvgd_stream_t stream) {
+    if (!X || !mask || bad_shape(n, p, p, w) || !aligned(X)) return MVGD_EINVAL;
+    const int64_t blocks = (n * p + 255) / 256;
+    k_block_zero_rows<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, (cudaStream_t)stream>>>(X, p, n, w, mask);
     return launch_status();
 }

@@ -80,18 +80,28 @@ class _Kit:
 
 
 def lowest_eigenpairs(op: api.Operator, nev: int, *, extra: int = 8, sigma: float = 1.0, tol: float = 1e-8,
-                      maxit: int = 200, rtol_solve: float = 1e-10, seed: int = 0, stream=None) -> EigResult:
-    """The nev smallest eigenvalues lambda of -L (op assembled in stored order)."""
+                      maxit: int = 200, rtol_solve: float = 1e-10, seed: int = 0, stream=None,
+                      boundary: torch.Tensor | None = None) -> EigResult:
+    """The nev smallest eigenvalues lambda of -L (op assembled in stored order).
+
+    boundary (uint8 [n], point order, as given to mvgd_dirichlet_rows on op): the
+    Dirichlet problem -- the spectrum of L on the interior points with v = 0 on the
+    boundary.  The basis is kept at zero on the boundary rows (a solve with zero
+    right-hand side there returns zero up to its tolerance; the rows are re-zeroed
+    after each solve, since A^-1 amplifies them by 1 / sigma against 1 / (sigma + lambda))."""
     p = ((nev + extra + W - 1) // W) * W
     if p > 64:
         raise ValueError("nev + extra must be at most 64")
     dev = op.col.device
     st = stream if stream is not None else torch.cuda.current_stream(dev)
+    mask = None
+    if boundary is not None:  # the mask in stored row order
+        mask = boundary[op.order.long()].contiguous() if op.order is not None else boundary.contiguous()
     with torch.cuda.stream(st):  # torch's copies and the library's calls on one stream
-        return _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed)
+        return _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask)
 
 
-def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed) -> EigResult:
+def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask) -> EigResult:
     n, dev = op.n, op.col.device
     # every vector stays in stored row order: the products read it so, and the
     # solves are told there is no point order to map from
@@ -103,6 +113,13 @@ def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed) -> EigResult:
     Y = _blocks(n, p, dev)
     Z = _blocks(n, p, dev)
     X.copy_(torch.from_numpy(np.random.default_rng(seed).standard_normal((p // W, n, W))))
+
+    def off_boundary(V):
+        if mask is not None:
+            LB.check("mvgd_block_zero_rows", L.mvgd_block_zero_rows(api._vp(V), p, n, W, api._vp(mask),
+                                                                    api._stream(st)))
+
+    off_boundary(X)
     kit.orthonormalize(X.clone(), X)
     prev = None
     change = np.inf
@@ -115,6 +132,7 @@ def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed) -> EigResult:
                 raise LB.MvgdError("mvgd_solve (shift-invert)", max(res.status))
             Y[b].copy_(res.u)
             solves += 1
+        off_boundary(Y)
         kit.orthonormalize(Y, X)
         mode = LB.SPMV_F64 if op.prec == LB.FP64 else LB.SPMV_F64_HILO  # FP64 (or hi + lo) weights
         for b in range(p // W):  # Z = L X

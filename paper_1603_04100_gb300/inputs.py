@@ -61,20 +61,25 @@ def random_sphere(n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(g / np.linalg.norm(g, axis=1, keepdims=True))
 
 
-def hemisphere(n: int, seed: int, rim: float = 2.0) -> tuple[np.ndarray, np.ndarray]:
-    """n uniform random points of the open upper unit hemisphere (z > 0) and a
-    boundary mask: the points within rim * sqrt(2 pi / n) of the rim z = 0, a band
-    about `rim` point spacings deep (uint8 [n], 1 = boundary)."""
+def hemisphere(n: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """n points of the upper unit hemisphere and its boundary mask: nb = round(sqrt(2 pi n) / 2)
+    points evenly spaced on the rim circle z = 0 (random phase; about the interior spacing
+    apart), flagged 1, then n - nb uniform random points with z > 0, flagged 0."""
     rng = _rng(seed)
+    nb = int(round(math.sqrt(2.0 * math.pi * n) / 2.0))
     out, have = [], 0
-    while have < n:
-        g = rng.standard_normal((2 * (n - have) + 64, 3))
+    while have < n - nb:
+        g = rng.standard_normal((2 * (n - nb - have) + 64, 3))
         g /= np.linalg.norm(g, axis=1, keepdims=True)
         g = g[g[:, 2] > 0.0]
         out.append(g)
         have += g.shape[0]
-    pts = np.ascontiguousarray(np.concatenate(out)[:n])
-    boundary = (pts[:, 2] < rim * math.sqrt(2.0 * math.pi / n)).astype(np.uint8)
+    inner = np.concatenate(out)[:n - nb]
+    t = (np.arange(nb) + rng.uniform()) * (2.0 * math.pi / nb)
+    rim = np.stack([np.cos(t), np.sin(t), np.zeros(nb)], axis=1)
+    pts = np.ascontiguousarray(np.concatenate([rim, inner]))
+    boundary = np.zeros(n, dtype=np.uint8)
+    boundary[:nb] = 1
     return pts, boundary
 
 

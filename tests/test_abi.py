@@ -87,6 +87,13 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
                            None) == LB.EINVAL                 # unknown row variant
     assert L.mvgd_row_signs(None, C.c_void_p(256), None) == LB.EINVAL
     assert L.mvgd_row_signs(C.byref(e), C.c_void_p(260), None) == LB.EINVAL  # counts not 8-byte aligned
+    # block sets: p not a multiple of w, X == Y, null mask
+    assert L.mvgd_block_gram(C.c_void_p(256), 7, C.c_void_p(512), 8, 100, 8, C.c_void_p(1024), C.c_void_p(2048),
+                             1 << 20, None) == LB.EINVAL
+    assert L.mvgd_block_combine(C.c_void_p(256), 8, C.c_void_p(1024), 8, 100, 8, C.c_void_p(256),
+                                None) == LB.EINVAL
+    assert L.mvgd_block_zero_rows(C.c_void_p(256), 8, 100, 8, None, None) == LB.EINVAL
+    assert L.mvgd_dirichlet_rows(None, C.c_void_p(256), None, None) == LB.EINVAL
     e4 = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
     assert L.mvgd_row_signs(C.byref(e4), C.c_void_p(256), None) == LB.EINVAL  # k < 5
     assert L.mvgd_spmv(C.byref(e), LB.SPMV_F32, 1, 1.0, 1.0, C.c_void_p(256), 0.0, C.c_void_p(512),

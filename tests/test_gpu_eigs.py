@@ -67,3 +67,23 @@ def test_lowest_eigenvalues_match_oracle(prec_name):
     assert abs(res.values[0]) <= 1e-8
     e2, _ = oracle.multiplet_errors(res.values, 4)
     assert e2 <= 0.02
+
+
+def test_dirichlet_hemisphere_eigenvalues_match_oracle():
+    dev = cuda_or_skip()
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300.eigs import lowest_eigenpairs
+    p, b = I.hemisphere(4000, 3)
+    pt = torch.from_numpy(p).to(dev)
+    bt = torch.from_numpy(b).to(dev)
+    nbr_t, ord_t = api.knn(pt, 20, want_order=True)
+    op = api.assemble(pt, nbr_t, prec=api.FP64, order=ord_t)
+    api.dirichlet_rows(op, bt)
+    res = lowest_eigenpairs(op, 10, boundary=bt)
+    assert res.change <= 1e-8, (res.iterations, res.change)
+    nbr = nbr_t.cpu().numpy()
+    val, _, _, _ = oracle.assemble(p, nbr)
+    want = oracle.lb_eigenvalues(oracle.dirichlet_rows(val, b), nbr, 10, boundary=b)
+    assert np.all(np.abs(res.values - want) <= 1e-6 * want), np.abs(res.values - want).max()
+    # l (l + 1) with multiplicity l
+    assert np.abs(res.values - np.array([2.0, 6, 6, 12, 12, 12, 20, 20, 20, 20])).max() <= 0.1

@@ -63,3 +63,17 @@ def test_random_sphere_errors_match_the_printed_table():
         assert np.all((ratio > 0.4) & (ratio < 2.5)), (ours, paper)
     # the error falls with the sampling density (about second order in h)
     assert e2[-1] < e2[0] / 4 and einf[-1] < einf[0] / 4
+
+
+def test_dirichlet_hemisphere_spectrum():
+    # v = 0 on the rim z = 0: the spherical harmonics odd in z, eigenvalue l (l + 1) with
+    # multiplicity l -- 2, 6 (x2), 12 (x3), 20 (x4); the error falls with the sampling density
+    want = np.array([2.0, 6, 6, 12, 12, 12, 20, 20, 20, 20])
+    errs = []
+    for n_pts in (4000, 16000):
+        p, b = I.hemisphere(n_pts, 3)
+        nbr = oracle.knn_grid(p, 20)
+        val, st, _, _ = oracle.assemble(p, nbr)
+        lam = oracle.lb_eigenvalues(oracle.dirichlet_rows(val, b), nbr, 10, boundary=b)
+        errs.append(np.abs(lam - want).max() / 20.0)
+    assert errs[0] < 5e-3 and errs[1] < errs[0] / 2, errs
