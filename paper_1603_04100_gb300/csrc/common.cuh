@@ -118,14 +118,14 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
 }
 
 // ---------------------------------------------------------------------------
-// Grid-wide barrier for persistent cooperative kernels.  Sense-reversing,
-// bounded: after `limit` polls it sets *err and returns false, so a kernel
-// whose blocks were not all resident ends with an error status instead of
-// spinning forever.
+// Grid-wide barrier for persistent cooperative kernels, on one monotonic
+// arrival counter.  Bounded: after `limit` polls it sets *err and returns
+// false, so a kernel whose blocks were not all resident ends with an error
+// status instead of spinning forever.
 // ---------------------------------------------------------------------------
 struct GridBarrier {
     unsigned int* count;   // zeroed before the launch
-    volatile unsigned int* gen;
+    volatile unsigned int* gen;  // unused (kept for the control-word layout)
 };
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const volatile unsigned* p) {
@@ -133,37 +133,32 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const volatile unsigned* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ void st_release_gpu(volatile unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add_gpu(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 of each block arrives with an acquire-release atomic (its block's
-// writes, ordered before it by __syncthreads, are released with it); the last
-// arrival resets the count and releases the new generation; the others poll
-// it with acquire loads (the error word every 256 polls).  About 2.3 us for
-// 456 blocks on GB300, against 3.6 us with fences and a sleeping poll.
-__device__ __forceinline__ bool grid_sync(GridBarrier b, int* err, long long limit) {
+// Thread 0 of each block adds its arrival with a release reduction (its
+// block's writes, ordered before it by __syncthreads, are released with it)
+// and does not wait for the add to return; it then polls the counter with
+// acquire loads until every block of this barrier has arrived: the e-th
+// barrier of a launch completes at count = e * gridDim.x (compared modulo
+// 2^32, so the counter may wrap).  One round trip less than a returning
+// atomic followed by a released generation word: about 1 us less per barrier
+// for 456 blocks on GB300.  `epoch` is the caller's count of barriers passed,
+// the same in every block.
+__device__ __forceinline__ bool grid_sync(GridBarrier b, unsigned& epoch, int* err, long long limit) {
     __syncthreads();
     bool ok = true;
+    epoch += 1u;
     if (threadIdx.x == 0) {
-        const unsigned my_gen = ld_acquire_gpu(b.gen);
-        const unsigned arrived = atom_add_acq_rel_gpu(b.count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            *(volatile unsigned*)b.count = 0;
-            st_release_gpu(b.gen, my_gen + 1u);
-        } else {
-            long long polls = 0;
-            while (ld_acquire_gpu(b.gen) == my_gen) {
-                if ((++polls & 255) == 0 && (polls > limit || *(volatile int*)err != 0)) {
-                    atomicCAS(err, 0, (int)MVGD_ETIMEOUT);
-                    ok = false;
-                    break;
-                }
+        const unsigned target = epoch * gridDim.x;
+        red_release_add_gpu(b.count, 1u);
+        long long polls = 0;
+        while ((int)(ld_acquire_gpu(b.count) - target) < 0) {
+            if ((++polls & 255) == 0 && (polls > limit || *(volatile int*)err != 0)) {
+                atomicCAS(err, 0, (int)MVGD_ETIMEOUT);
+                ok = false;
+                break;
             }
         }
     }

@@ -828,6 +828,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     float c1[QT], c2[QT];
     // the request whose state S holds, while no phase has advanced it since
     int held = -1;
+    unsigned bar_epoch = 0;  // grid barriers passed (the same count in every block)
     // Loads request ri's per-RHS state into S (block-wide) and its masks.
     auto enter = [&](int ri, int ph) {
         held = ri;
@@ -955,7 +956,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
             *ctl.stop = 1;
         if (reduce) held = -1;  // the states were advanced at the arrivals
-        const bool ok = grid_sync(ctl.bar, ctl.err, ctl.limit);
+        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit);
         trace_step(ctl, (unsigned)ph);
         return ok;
     };
@@ -1087,7 +1088,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 }
             }
         }
-        const bool ok = grid_sync(ctl.bar, ctl.err, ctl.limit);
+        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit);
         trace_step(ctl, 0x1000u | ((unsigned)side << 8) | ((unsigned)kind << 4) | (unsigned)l);
         return ok;
     };
