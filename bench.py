@@ -39,9 +39,9 @@ N_DEFAULT, K_DEFAULT, SEED = 1_048_576, 20, 0
 RTOL = 1e-8
 # DRAM bytes (read + write) per iteration of k_solve<1,1,1> on the bench workload
 # (N = 1,048,576, K = 20, multigrid, FP32 inner): an ncu capture of a 20-iteration
-# launch of the current kernel read 21.51 GB and wrote 0.65 GB.  Valid for this
+# launch of the current kernel read 21.513 GB and wrote 0.645 GB.  Valid for this
 # kernel and workload only; any other path or size reports traffic null.
-KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = (21.515e9 + 0.646e9) / 20
+KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = (21.513e9 + 0.645e9) / 20
 BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see run_batched)
 WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
             "6 nearest, u = 5z^3-3z, f = 13u, (I-L)u = f to 1e-8 relative residual")
