@@ -289,6 +289,34 @@ def lb_eigen_stats(k, stream, n_pts: int = 16000):
             "paper_random_16000_pct": {"E2_lambda4": 0.069, "Einf_lambda4": 0.13}}
 
 
+def gs_spectral_stats(k, stream, n_pts: int = 16000, iters: int = 300):
+    """Sec. 4.1 on a random sphere: the spectral radius of the Gauss-Seidel iteration
+    matrix of I - L (stored row order) for the MVGD rows and for the least-squares
+    comparator, by mvgd_gs_power (geometric mean of the norm ratios over the second
+    half of the steps), timed with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300 import inputs as I
+    p = I.random_sphere(n_pts, 1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pt = torch.from_numpy(p).to(dev)
+    x0 = torch.from_numpy(np.random.default_rng(0).standard_normal(n_pts)).to(dev)
+    out = {"n": n_pts, "k": k, "iters": iters, "sigma": 1.0, "order": "stored (Z-order)"}
+    with torch.cuda.stream(stream):
+        nbr, order = api.knn(pt, k, want_order=True, stream=stream)
+        for nm, variant in (("mvgd", api.ROW_MVGD), ("least_squares", api.ROW_LS)):
+            op = api.assemble(pt, nbr, prec=api.FP64, order=order, variant=variant, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = api.gs_power(op, x0, iters, sigma=1.0, stream=stream)
+            e1.record(stream)
+            stream.synchronize()
+            out[nm] = {"rho": g.rho, "nu_last": float(g.nu[-1]), "status": g.status, "ms": e0.elapsed_time(e1),
+                       "us_per_step": 1e3 * e0.elapsed_time(e1) / iters}
+    return out
+
+
 def amg_coarse_bytes(H, n: int) -> float:
     """Bytes per fine row that one V-cycle moves on levels >= 1: per level, down
     and up read each stored entry (int32 column + FP32 value) once, plus about
@@ -654,6 +682,7 @@ def main():
     line["row_signs"] = row_sign_stats(pts, mixed, k, flush, stream)
     line["dirichlet_hemisphere"] = dirichlet_hemisphere(n, k, flush, stream)
     line["lb_eigenvalues"] = lb_eigen_stats(k, stream)
+    line["gauss_seidel_spectral_radius"] = gs_spectral_stats(k, stream)
 
     if not args.no_e2e:
         pts_h = torch.from_numpy(pr.pts).pin_memory()

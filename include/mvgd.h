@@ -232,6 +232,37 @@ mvgd_status mvgd_block_zero_rows(double *X, int32_t p, int64_t n, int32_t w, con
                                  mvgd_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Conditioning of the stored system (Sec. 4.1): the Gauss-Seidel iteration
+ * matrix T = M^-1 N of A = sigma I - L, split A = M + N with M the lower
+ * triangle including the diagonal and N the strictly upper triangle, both in
+ * STORED row order (the order the operator's rows are kept in).  A Gauss-Seidel
+ * sweep converges from every start iff the spectral radius of T is below 1.
+ *
+ * mvgd_gs_power runs `iters` steps of the power iteration
+ *   x_0 = x0 / ||x0||_2,   y_t = T x_t,   nu[t] = ||y_t||_2,   x_{t+1} = y_t / nu[t]
+ * in one cooperative launch.  nu[t] tends to |lambda_max(T)| when that
+ * eigenvalue is real and simple; with a complex pair (or +-lambda) on top, nu
+ * oscillates and the geometric mean of nu over a window converges instead.
+ * Each T x is N x followed by the forward substitution M y = N x: warps take
+ * rows in increasing order from a ticket counter, and a row waits (bounded) on
+ * a flag of each lower neighbour written by the warp that computed it, so
+ * there is no level schedule; every row's sums are over its own slots in slot
+ * order, and the norms are reduced in a fixed order, so results repeat bit for
+ * bit.  A neighbour column equal to the row itself adds to the diagonal.
+ *   L       the operator (MVGD_FP64, or FP32_REFINE read as hi + lo in FP64)
+ *   x0      DEVICE double [n], stored order, not all zero
+ *   nu      DEVICE double [iters] out
+ *   x       DEVICE double [n] out: x_iters (unit norm), stored order; may be x0
+ *   status  DEVICE int32 [1] out: MVGD_OK, MVGD_ENONFINITE (zero or non-finite
+ *           norm: a zero diagonal of A, or x0 = 0) or MVGD_ETIMEOUT (a bounded
+ *           wait gave up)
+ * Workspace: mvgd_gs_power_workspace_bytes(n, iters).  1 <= iters <= 2^20;
+ * n < 2^31. */
+size_t mvgd_gs_power_workspace_bytes(int64_t n, int32_t iters);
+mvgd_status mvgd_gs_power(const mvgd_ell *L, double sigma, const double *x0, int32_t iters, double *nu, double *x,
+                          int32_t *status, void *workspace, size_t workspace_bytes, mvgd_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Operator application (the product every Krylov step repeats, Sec. 3.1 and
  * Sec. 4.2):  y = alpha * (sigma x - L x) + beta * y  for nrhs right-hand
  * sides stored interleaved, x and y [n][nrhs] in STORED row order.

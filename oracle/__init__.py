@@ -20,6 +20,8 @@ the paper they follow):
 * ``lb_eigenvalues``, ``multiplet_errors``: the lowest LB eigenvalues and the
   error measures of Sec. 4.3.
 * ``normal_matrix``: the 6x6 normal-equation matrix of Sec. 2 as printed.
+* ``system_matrix``, ``gs_eigenvalues``, ``gs_power``: sigma I - L in a given
+  row order and the spectrum of its Gauss-Seidel iteration matrix (Sec. 4.1).
 """
 from __future__ import annotations
 
@@ -213,6 +215,43 @@ def multiplet_errors(lams, n: int) -> tuple:
     lam = n * (n + 1.0)
     r = (np.asarray(lams, dtype=np.float64)[n * n:n * n + 2 * n + 1] - lam) / lam
     return float(np.sqrt(np.mean(r * r))), float(np.abs(r).max())
+
+
+def system_matrix(val, nbr, sigma: float = 1.0, order=None):
+    """sigma I - L as scipy CSR with rows and columns in stored order: stored row r
+    is point order[r] (order None: point r), so the result is P (sigma I - L) P^T."""
+    import scipy.sparse as sp
+    A = (sigma * sp.identity(nbr.shape[0], format="csr") - to_csr(val, nbr)).tocsr()
+    if order is not None:
+        o = np.asarray(order, dtype=np.int64)
+        A = A[o][:, o].tocsr()
+    return A
+
+
+def gs_eigenvalues(A) -> np.ndarray:
+    """Eigenvalues of the Gauss-Seidel iteration matrix M^-1 N of A (Sec. 4.1), where
+    A = M + N with N the strictly upper triangle of A.  Dense: small n only."""
+    import scipy.linalg as sl
+    Ad = A.toarray() if hasattr(A, "toarray") else np.asarray(A, dtype=np.float64)
+    T = sl.solve_triangular(np.tril(Ad), np.triu(Ad, 1), lower=True)
+    return np.linalg.eigvals(T)
+
+
+def gs_power(A, x0, iters: int) -> tuple:
+    """Power iteration on M^-1 N (Sec. 4.1): x_0 = x0 / ||x0||, y_t = M^-1 (N x_t),
+    nu_t = ||y_t||, x_{t+1} = y_t / nu_t.  Returns (nu [iters], x_iters)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    A = sp.csr_matrix(A)
+    M = sp.tril(A, 0, format="csr")
+    N = sp.triu(A, 1, format="csr")
+    x = np.asarray(x0, dtype=np.float64) / np.linalg.norm(x0)
+    nu = np.empty(iters)
+    for t in range(iters):
+        y = spl.spsolve_triangular(M, N @ x, lower=True)
+        nu[t] = np.linalg.norm(y)
+        x = y / nu[t]
+    return nu, x
 
 
 def normal_matrix(x, y) -> np.ndarray:

@@ -185,6 +185,33 @@ def dirichlet_rows(op: Operator, boundary: torch.Tensor, stream=None) -> int:
 
 
 @dataclass
+class GsPower:
+    nu: np.ndarray        # [iters] ||T x_t|| for unit x_t
+    x: torch.Tensor       # the last unit iterate, stored order
+    status: int
+    rho: float            # geometric mean of nu over the second half of the steps
+
+
+def gs_power(op: Operator, x0: torch.Tensor, iters: int, sigma: float = 1.0, stream=None) -> GsPower:
+    """Power iteration on the Gauss-Seidel iteration matrix of sigma I - L in stored
+    row order (mvgd_gs_power, Sec. 4.1).  x0: double [n], stored order."""
+    _require_cuda(x0, torch.float64, "x0")
+    L = LB.load()
+    dev = op.col.device
+    nu = torch.empty(iters, dtype=torch.float64, device=dev)
+    x = torch.empty(op.n, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(L.mvgd_gs_power_workspace_bytes(op.n, iters), dtype=torch.uint8, device=dev)
+    c = op.cstruct()
+    LB.check("mvgd_gs_power", L.mvgd_gs_power(C.byref(c), sigma, _vp(x0), iters, _vp(nu), _vp(x), _vp(status),
+                                               _vp(ws), ws.numel(), _stream(stream)))
+    nu_h = nu.cpu().numpy()
+    tail = nu_h[iters // 2:]
+    rho = float(np.exp(np.mean(np.log(tail)))) if np.all(tail > 0) else float("nan")
+    return GsPower(nu=nu_h, x=x, status=int(status.item()), rho=rho)
+
+
+@dataclass
 class SolveResult:
     u: torch.Tensor
     iters: list

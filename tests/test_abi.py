@@ -94,6 +94,14 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
                                 None) == LB.EINVAL
     assert L.mvgd_block_zero_rows(C.c_void_p(256), 8, 100, 8, None, None) == LB.EINVAL
     assert L.mvgd_dirichlet_rows(None, C.c_void_p(256), None, None) == LB.EINVAL
+    # Gauss-Seidel power iteration: no steps, no status word, a NaN shift, too small a workspace
+    assert L.mvgd_gs_power_workspace_bytes(100, 0) == 0
+    assert L.mvgd_gs_power_workspace_bytes(100, 10) >= 2 * 8 * 100 + 4 * 100 + 4 * 10
+    gs = (C.c_void_p(256), 10, C.c_void_p(512), C.c_void_p(768), C.c_void_p(1024), C.c_void_p(2048), 1 << 20, None)
+    assert L.mvgd_gs_power(C.byref(e), 1.0, gs[0], 0, *gs[2:]) == LB.EINVAL
+    assert L.mvgd_gs_power(C.byref(e), 1.0, *gs[:4], None, *gs[5:]) == LB.EINVAL
+    assert L.mvgd_gs_power(C.byref(e), float("nan"), *gs) == LB.EINVAL
+    assert L.mvgd_gs_power(C.byref(e), 1.0, *gs[:6], 64, None) == LB.EWORKSPACE
     e4 = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
     assert L.mvgd_row_signs(C.byref(e4), C.c_void_p(256), None) == LB.EINVAL  # k < 5
     assert L.mvgd_spmv(C.byref(e), LB.SPMV_F32, 1, 1.0, 1.0, C.c_void_p(256), 0.0, C.c_void_p(512),
