@@ -61,12 +61,14 @@ def random_sphere(n: int, seed: int) -> np.ndarray:
     return np.ascontiguousarray(g / np.linalg.norm(g, axis=1, keepdims=True))
 
 
-def hemisphere(n: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
-    """n points of the upper unit hemisphere and its boundary mask: nb = round(sqrt(2 pi n) / 2)
-    points evenly spaced on the rim circle z = 0 (random phase; about the interior spacing
-    apart), flagged 1, then n - nb uniform random points with z > 0, flagged 0."""
+def hemisphere(n: int, seed: int, nb: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """n points of the upper unit hemisphere and its boundary mask: nb points (default
+    round(sqrt(2 pi n) / 2), about the interior spacing apart) evenly spaced on the rim
+    circle z = 0 with a random phase, flagged 1, then n - nb uniform random points with
+    z > 0, flagged 0."""
     rng = _rng(seed)
-    nb = int(round(math.sqrt(2.0 * math.pi * n) / 2.0))
+    if nb is None:
+        nb = int(round(math.sqrt(2.0 * math.pi * n) / 2.0))
     out, have = [], 0
     while have < n - nb:
         g = rng.standard_normal((2 * (n - nb - have) + 64, 3))
