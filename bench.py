@@ -259,6 +259,42 @@ def dirichlet_hemisphere(n, k, flush, stream):
     return out
 
 
+def neumann_hemisphere(n, k, flush, stream):
+    """Open surface with dU/dn = 0 on the rim (Sec. 3.1, reflection method): the upper
+    hemisphere with n points, u = x, (I - L) u = 3x on the interior points; kNN of the
+    cloud, ghosts, kNN and assembly over interior points and ghosts, fold, multigrid
+    set-up and the FP32 + FP64-refinement solve, timed once with CUDA events (L2 flushed)."""
+    import numpy as np
+    import torch
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300 import inputs as I
+    p, b = I.hemisphere(n, 5)
+    dev = flush.device
+    pts = torch.from_numpy(p).to(dev)
+    bt = torch.from_numpy(b).to(dev)
+    out = {}
+    for rep in range(2):  # the first pass warms up
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            op, cloud = api.neumann_operator(pts, bt, k, prec=api.FP32_REFINE, stream=stream)
+            x = pts[cloud.interior.long(), 0].contiguous()
+            f = 3.0 * x
+            ev[1].record(stream)
+            res = api.solve(op, f, rtol=RTOL, precond=2, stream=stream)
+            ev[2].record(stream)
+        stream.synchronize()
+        u = res.u.cpu().numpy()
+        xs = x.cpu().numpy()
+        out = {"n": n, "k": k, "boundary_points": cloud.n_boundary, "interior_rows": cloud.n_interior,
+               "ghosts": cloud.n_ghost, "ms": ev[0].elapsed_time(ev[2]), "setup_ms": ev[0].elapsed_time(ev[1]),
+               "solve_ms": ev[1].elapsed_time(ev[2]), "iters": res.iters[0], "status": res.status[0],
+               "relres": res.relres[0], "err_exact_inf": float(np.abs(u - xs).max()),
+               "points_per_s": n / (ev[0].elapsed_time(ev[2]) * 1e-3)}
+    return out
+
+
 def lb_eigen_stats(k, stream, n_pts: int = 16000):
     """Sec. 4.3 on the paper's largest random sphere: the 25 smallest eigenvalues of -L
     (lambda_0 .. lambda_4 multiplets) by the shift-invert subspace iteration, timed with
@@ -681,6 +717,7 @@ def main():
     line["spmv"] = spmv_roofline(results, n, k, flush, stream, peak, peak_kind)
     line["row_signs"] = row_sign_stats(pts, mixed, k, flush, stream)
     line["dirichlet_hemisphere"] = dirichlet_hemisphere(n, k, flush, stream)
+    line["neumann_hemisphere"] = neumann_hemisphere(n, k, flush, stream)
     line["lb_eigenvalues"] = lb_eigen_stats(k, stream)
     line["gauss_seidel_spectral_radius"] = gs_spectral_stats(k, stream)
 

@@ -209,6 +209,59 @@ mvgd_status mvgd_row_signs(const mvgd_ell *L, int64_t *counts, mvgd_stream_t str
  * Asynchronous; MVGD_EINVAL on a null operator or mask, or out-of-range sizes. */
 mvgd_status mvgd_dirichlet_rows(mvgd_ell *L, const uint8_t *boundary, int32_t *count, mvgd_stream_t stream);
 
+/* Neumann boundary by reflection (Sec. 3.1), homogeneous condition dU/dn = 0.
+ * The unknowns are the interior points.  An interior point whose K nearest
+ * neighbours include a boundary point is mirrored through the boundary at its
+ * closest boundary point p_b (key: squared distance, then index), in the frame
+ *   e2 = surface normal at p_b (smallest eigenvector of the covariance of p_b's
+ *        K neighbours), e1 = boundary tangent at p_b (quadratic fit of the curve
+ *        through p_b and its kb nearest boundary points, along their principal
+ *        axis), made orthogonal to e2, e3 = e1 x e2;
+ * the ghost is p - 2 ((p - p_b).e3) e3.  Three calls make the operator:
+ *   1. mvgd_neumann_ghosts writes the cloud Q = interior points (point order)
+ *      followed by the ghosts (in the order of the points they mirror);
+ *   2. mvgd_knn and mvgd_assemble run on Q (any stored order);
+ *   3. mvgd_neumann_fold keeps the interior rows of Q's operator, in its stored
+ *      order, and maps every column to the interior point it stands for; a
+ *      column may then repeat, or equal its own row (a point next to its ghost).
+ * The folded operator's rows sum to zero as before, so every product, solve,
+ * multigrid set-up and eigensolver call takes it as it is.
+ *
+ * mvgd_neumann_ghosts:
+ *   pts [n][3], nbr [n][k] (mvgd_knn of the whole cloud), boundary uint8 [n]:
+ *            DEVICE, point order
+ *   kb       boundary neighbours of the tangent fit, 2 <= kb <= 16 (fewer when
+ *            the boundary has fewer points)
+ *   q        DEVICE double [2 n][3] out: Q, n_interior + n_ghost rows written
+ *   q_src    DEVICE int32 [2 n] out: the interior position each point of Q
+ *            stands for (itself for the interior points)
+ *   interior DEVICE int32 [n] out: point index of each interior position
+ *   ghost_bnd, ghost_dist  DEVICE int32 / double [n] out: per ghost, the
+ *            boundary point used and |p - ghost| (for an inhomogeneous
+ *            condition U(ghost) = U(p) + |p - ghost| g(p_b))
+ *   counts   DEVICE int32 [4] out: n_interior, n_ghost, n_boundary, and the
+ *            boundary points whose frame failed (fewer than 3 boundary points,
+ *            a singular tangent fit, e1 parallel to e2; their e3 is zero, so
+ *            their ghosts coincide with their points)
+ * Workspace mvgd_neumann_ghosts_workspace_bytes(n).  Asynchronous.
+ *
+ * mvgd_neumann_fold:
+ *   LQ       Q's operator (n = n_interior + n_ghost, optional order)
+ *   q_src    as written by mvgd_neumann_ghosts
+ *   LI       out: n = n_interior, the same k and prec as LQ, arrays from
+ *            mvgd_ell_bytes(n_interior, ...); LI->order must point to DEVICE
+ *            int32 [n_interior] that the call fills (stored row -> interior
+ *            position).  Padding rows get zero weights and column 0.
+ * Workspace mvgd_neumann_fold_workspace_bytes(LQ->n).  Asynchronous. */
+size_t mvgd_neumann_ghosts_workspace_bytes(int64_t n);
+mvgd_status mvgd_neumann_ghosts(const double *pts, int64_t n, int32_t k, const int32_t *nbr,
+                                const uint8_t *boundary, int32_t kb, double *q, int32_t *q_src, int32_t *interior,
+                                int32_t *ghost_bnd, double *ghost_dist, int32_t *counts, void *workspace,
+                                size_t workspace_bytes, mvgd_stream_t stream);
+size_t mvgd_neumann_fold_workspace_bytes(int64_t nq);
+mvgd_status mvgd_neumann_fold(const mvgd_ell *LQ, const int32_t *q_src, mvgd_ell *LI, void *workspace,
+                              size_t workspace_bytes, mvgd_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Sets of vectors, for the subspace iteration behind the lowest eigenpairs of
  * the LB operator (Sec. 4.3).  A set of p vectors of length n (FP64, DEVICE,

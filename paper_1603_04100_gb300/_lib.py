@@ -29,6 +29,8 @@ EXPORTS = (
     "mvgd_amg_apply_workspace_bytes", "mvgd_amg_apply", "mvgd_trace_enable", "mvgd_trace_read",
     "mvgd_row_signs", "mvgd_dirichlet_rows", "mvgd_block_gram_workspace_bytes", "mvgd_block_gram",
     "mvgd_block_combine", "mvgd_block_zero_rows", "mvgd_gs_power_workspace_bytes", "mvgd_gs_power",
+    "mvgd_neumann_ghosts_workspace_bytes", "mvgd_neumann_ghosts", "mvgd_neumann_fold_workspace_bytes",
+    "mvgd_neumann_fold",
 )
 PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
 AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
@@ -161,6 +163,15 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_gs_power_workspace_bytes.restype = C.c_size_t
     L.mvgd_gs_power.argtypes = [C.POINTER(Ell), C.c_double, _P, C.c_int32, _P, _P, _P, _P, C.c_size_t, _P]
     L.mvgd_gs_power.restype = C.c_int
+    L.mvgd_neumann_ghosts_workspace_bytes.argtypes = [C.c_int64]
+    L.mvgd_neumann_ghosts_workspace_bytes.restype = C.c_size_t
+    L.mvgd_neumann_ghosts.argtypes = [_P, C.c_int64, C.c_int32, _P, _P, C.c_int32, _P, _P, _P, _P, _P, _P, _P,
+                                      C.c_size_t, _P]
+    L.mvgd_neumann_ghosts.restype = C.c_int
+    L.mvgd_neumann_fold_workspace_bytes.argtypes = [C.c_int64]
+    L.mvgd_neumann_fold_workspace_bytes.restype = C.c_size_t
+    L.mvgd_neumann_fold.argtypes = [C.POINTER(Ell), _P, C.POINTER(Ell), _P, C.c_size_t, _P]
+    L.mvgd_neumann_fold.restype = C.c_int
     _lib = L
     return L
 

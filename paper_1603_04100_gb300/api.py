@@ -185,6 +185,75 @@ def dirichlet_rows(op: Operator, boundary: torch.Tensor, stream=None) -> int:
 
 
 @dataclass
+class NeumannCloud:
+    """Interior points and ghosts of a Neumann boundary (mvgd_neumann_ghosts, Sec. 3.1)."""
+    q: torch.Tensor           # [n_interior + n_ghost][3]: interior points, then ghosts
+    q_src: torch.Tensor       # int32 [n_interior + n_ghost]: the interior position each stands for
+    interior: torch.Tensor    # int32 [n_interior]: point index of each interior position
+    ghost_bnd: torch.Tensor   # int32 [n_ghost]: the boundary point each ghost was mirrored at
+    ghost_dist: torch.Tensor  # [n_ghost]: |point - ghost|
+    n_interior: int
+    n_ghost: int
+    n_boundary: int
+    bad_frames: int
+
+
+def neumann_ghosts(pts: torch.Tensor, nbr: torch.Tensor, boundary: torch.Tensor, kb: int = 6,
+                   stream=None) -> NeumannCloud:
+    """The ghosts of the interior points next to the boundary (mvgd_neumann_ghosts).
+    pts, nbr (mvgd_knn of the whole cloud) and boundary (uint8) in point order."""
+    _require_cuda(pts, torch.float64, "pts")
+    _require_cuda(nbr, torch.int32, "nbr")
+    _require_cuda(boundary, torch.uint8, "boundary")
+    L = LB.load()
+    n, k = nbr.shape
+    dev = pts.device
+    q = torch.empty((2 * n, 3), dtype=torch.float64, device=dev)
+    q_src = torch.empty(2 * n, dtype=torch.int32, device=dev)
+    interior = torch.empty(n, dtype=torch.int32, device=dev)
+    gb = torch.empty(n, dtype=torch.int32, device=dev)
+    gd = torch.empty(n, dtype=torch.float64, device=dev)
+    counts = torch.zeros(4, dtype=torch.int32, device=dev)
+    ws = torch.empty(L.mvgd_neumann_ghosts_workspace_bytes(n), dtype=torch.uint8, device=dev)
+    LB.check("mvgd_neumann_ghosts", L.mvgd_neumann_ghosts(_vp(pts), n, k, _vp(nbr), _vp(boundary), kb, _vp(q),
+                                                           _vp(q_src), _vp(interior), _vp(gb), _vp(gd),
+                                                           _vp(counts), _vp(ws), ws.numel(), _stream(stream)))
+    ni, ng, nb, bad = (int(v) for v in counts.cpu().tolist())
+    return NeumannCloud(q=q[:ni + ng], q_src=q_src[:ni + ng], interior=interior[:ni], ghost_bnd=gb[:ng],
+                        ghost_dist=gd[:ng], n_interior=ni, n_ghost=ng, n_boundary=nb, bad_frames=bad)
+
+
+def neumann_fold(op_q: Operator, cloud: NeumannCloud, stream=None) -> Operator:
+    """The interior rows of the operator assembled on cloud.q, every ghost column
+    mapped to its point (mvgd_neumann_fold).  The result's order maps stored rows to
+    interior positions, so its point order is the interior order of the cloud."""
+    L = LB.load()
+    dev = op_q.col.device
+    ni = cloud.n_interior
+    col, val, lo = ell_alloc(ni, op_q.k, op_q.prec, dev)
+    out = Operator(ni, op_q.k, op_q.prec, col, val, lo, torch.empty(ni, dtype=torch.int32, device=dev))
+    ws = torch.empty(L.mvgd_neumann_fold_workspace_bytes(op_q.n), dtype=torch.uint8, device=dev)
+    cq, ci = op_q.cstruct(), out.cstruct()
+    LB.check("mvgd_neumann_fold", L.mvgd_neumann_fold(C.byref(cq), _vp(cloud.q_src), C.byref(ci), _vp(ws),
+                                                       ws.numel(), _stream(stream)))
+    return out
+
+
+def neumann_operator(pts: torch.Tensor, boundary: torch.Tensor, k: int, *, kb: int = 6, prec: int = FP64,
+                     stream=None) -> tuple:
+    """The MVGD operator of an open surface with dU/dn = 0 on its boundary (Sec. 3.1):
+    kNN of the cloud, ghosts, kNN and assembly over interior points and ghosts, fold.
+    Returns (operator over the interior points, NeumannCloud)."""
+    nbr = knn(pts, k, stream=stream)
+    cloud = neumann_ghosts(pts, nbr, boundary, kb, stream=stream)
+    if cloud.bad_frames:
+        raise LB.MvgdError("mvgd_neumann_ghosts", LB.EDEGENERATE)
+    nq, oq = knn(cloud.q, k, want_order=True, stream=stream)
+    op_q = assemble(cloud.q, nq, prec=prec, order=oq, stream=stream)
+    return neumann_fold(op_q, cloud, stream=stream), cloud
+
+
+@dataclass
 class GsPower:
     nu: np.ndarray        # [iters] ||T x_t|| for unit x_t
     x: torch.Tensor       # the last unit iterate, stored order

@@ -102,6 +102,19 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
     assert L.mvgd_gs_power(C.byref(e), 1.0, *gs[:4], None, *gs[5:]) == LB.EINVAL
     assert L.mvgd_gs_power(C.byref(e), float("nan"), *gs) == LB.EINVAL
     assert L.mvgd_gs_power(C.byref(e), 1.0, *gs[:6], 64, None) == LB.EWORKSPACE
+    # Neumann ghosts: kb below 2, no counts word, too small a workspace; fold: k or order mismatch
+    assert L.mvgd_neumann_ghosts_workspace_bytes(1) == 0 and L.mvgd_neumann_ghosts_workspace_bytes(100) > 24 * 100
+    ng = [C.c_void_p(256), 100, 10, C.c_void_p(512), C.c_void_p(768), 6] + [C.c_void_p(1024 * (i + 1)) for i in range(6)]
+    assert L.mvgd_neumann_ghosts(*ng[:5], 1, *ng[6:], C.c_void_p(8192), 1 << 20, None) == LB.EINVAL
+    assert L.mvgd_neumann_ghosts(*ng[:11], None, C.c_void_p(8192), 1 << 20, None) == LB.EINVAL
+    assert L.mvgd_neumann_ghosts(*ng, C.c_void_p(8192), 64, None) == LB.EWORKSPACE
+    eq = LB.Ell(120, 10, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
+    ei = LB.Ell(100, 12, LB.FP64, C.c_void_p(4096), C.c_void_p(1024), C.c_void_p(2048), None)
+    assert L.mvgd_neumann_fold(C.byref(eq), C.c_void_p(768), C.byref(ei), C.c_void_p(8192), 1 << 20,
+                               None) == LB.EINVAL
+    ei = LB.Ell(100, 10, LB.FP64, None, C.c_void_p(1024), C.c_void_p(2048), None)
+    assert L.mvgd_neumann_fold(C.byref(eq), C.c_void_p(768), C.byref(ei), C.c_void_p(8192), 1 << 20,
+                               None) == LB.EINVAL
     e4 = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
     assert L.mvgd_row_signs(C.byref(e4), C.c_void_p(256), None) == LB.EINVAL  # k < 5
     assert L.mvgd_spmv(C.byref(e), LB.SPMV_F32, 1, 1.0, 1.0, C.c_void_p(256), 0.0, C.c_void_p(512),
