@@ -29,17 +29,24 @@ from . import api
 W = 8  # columns per block: the solver's right-hand-side limit
 
 
+def _rows(n: int) -> int:
+    """Rows of a block: n rounded up to a multiple of 4, so that every block of
+    8 FP64 columns starts on the 256-byte boundary the library's entry points
+    require; the extra rows stay zero and add nothing to any Gram matrix."""
+    return (n + 3) // 4 * 4
+
+
 @dataclass
 class EigResult:
     values: np.ndarray      # the nev smallest lambda, ascending
-    vectors: torch.Tensor   # [p/8][n][8] orthonormal basis of the converged subspace (stored order)
+    vectors: torch.Tensor   # [p/8][n][8] orthonormal basis of the converged subspace (stored order; a view)
     iterations: int
     change: float           # largest relative change of the nev values in the last iteration
     solves: int             # mvgd_solve calls made
 
 
 def _blocks(n: int, p: int, device) -> torch.Tensor:
-    return torch.empty((p // W, n, W), dtype=torch.float64, device=device)
+    return torch.zeros((p // W, _rows(n), W), dtype=torch.float64, device=device)
 
 
 class _Kit:
@@ -47,7 +54,7 @@ class _Kit:
 
     def __init__(self, n: int, p: int, device, stream):
         self.L = LB.load()
-        self.n, self.p, self.dev = n, p, device
+        self.n, self.p, self.dev = _rows(n), p, device
         self.s = api._stream(stream)
         self.ws = torch.empty(self.L.mvgd_block_gram_workspace_bytes(p, p), dtype=torch.uint8, device=device)
         self.G = torch.empty((p, p), dtype=torch.float64, device=device)
@@ -95,8 +102,10 @@ def lowest_eigenpairs(op: api.Operator, nev: int, *, extra: int = 8, sigma: floa
     dev = op.col.device
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     mask = None
-    if boundary is not None:  # the mask in stored row order
-        mask = boundary[op.order.long()].contiguous() if op.order is not None else boundary.contiguous()
+    if boundary is not None:  # the mask in stored row order, padded like the blocks
+        m = boundary[op.order.long()] if op.order is not None else boundary
+        mask = torch.zeros(_rows(op.n), dtype=torch.uint8, device=m.device)
+        mask[:op.n] = m
     with torch.cuda.stream(st):  # torch's copies and the library's calls on one stream
         return _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask)
 
@@ -112,11 +121,11 @@ def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask) -> EigRe
     X = _blocks(n, p, dev)
     Y = _blocks(n, p, dev)
     Z = _blocks(n, p, dev)
-    X.copy_(torch.from_numpy(np.random.default_rng(seed).standard_normal((p // W, n, W))))
+    X[:, :n].copy_(torch.from_numpy(np.random.default_rng(seed).standard_normal((p // W, n, W))))
 
     def off_boundary(V):
         if mask is not None:
-            LB.check("mvgd_block_zero_rows", L.mvgd_block_zero_rows(api._vp(V), p, n, W, api._vp(mask),
+            LB.check("mvgd_block_zero_rows", L.mvgd_block_zero_rows(api._vp(V), p, kit.n, W, api._vp(mask),
                                                                     api._stream(st)))
 
     off_boundary(X)
@@ -127,18 +136,18 @@ def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask) -> EigRe
     it = 0
     for it in range(1, maxit + 1):
         for b in range(p // W):  # Y = (sigma I - L)^-1 X
-            res = api.solve(op, X[b], rtol=rtol_solve, amg=H_amg, stream=st)
+            res = api.solve(op, X[b, :n], rtol=rtol_solve, amg=H_amg, stream=st)
             if any(s != LB.OK for s in res.status):
                 raise LB.MvgdError("mvgd_solve (shift-invert)", max(res.status))
-            Y[b].copy_(res.u)
+            Y[b, :n].copy_(res.u)
             solves += 1
         off_boundary(Y)
         kit.orthonormalize(Y, X)
         mode = LB.SPMV_F64 if op.prec == LB.FP64 else LB.SPMV_F64_HILO  # FP64 (or hi + lo) weights
         for b in range(p // W):  # Z = L X
             c = op.cstruct()
-            LB.check("mvgd_spmv", L.mvgd_spmv(C.byref(c), mode, W, 0.0, -1.0, api._vp(X[b]), 0.0,
-                                                api._vp(Z[b]), api._stream(st)))
+            LB.check("mvgd_spmv", L.mvgd_spmv(C.byref(c), mode, W, 0.0, -1.0, api._vp(X[b, :n]), 0.0,
+                                                api._vp(Z[b, :n]), api._stream(st)))
         Hm = kit.gram(X, Z)
         theta = np.linalg.eigvals(Hm)
         lam = np.sort(-theta.real)[:nev]
@@ -147,4 +156,4 @@ def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask) -> EigRe
             if change <= tol:
                 break
         prev = lam
-    return EigResult(values=lam, vectors=X, iterations=it, change=change, solves=solves)
+    return EigResult(values=lam, vectors=X[:, :n], iterations=it, change=change, solves=solves)
