@@ -559,15 +559,14 @@ def main():
         run_served(args)
         return
     import torch
-    import torch.distributed as dist
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
+    from paper_1603_04100_gb300.replicas import Replicas
+
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    reps = Replicas("nccl", dev)
+    rank, world = reps.rank, reps.world
 
     from paper_1603_04100_gb300 import api, build
     from paper_1603_04100_gb300 import inputs as I
@@ -581,10 +580,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(1 << 30, dtype=torch.uint8, device=dev)  # also outlasts the host's first launches
 
-    def barrier():
-        torch.cuda.synchronize(dev)
-        if world > 1:
-            dist.barrier()
+    barrier = reps.barrier
 
     def timed_runs(pipe, steps, warmup):
         """Per-step CUDA-event times of knn / assembly / solve on the pipeline's stream."""
@@ -610,12 +606,7 @@ def main():
                         ev[3].elapsed_time(ev[4])))
         return out, wall
 
-    def max_over_ranks(ms):
-        if world == 1:
-            return ms
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = reps.max
 
     # Precision strategies (FP32 inner + FP64 refinement, or plain FP64) times
     # preconditioners (row abs-sum scaling, or one multigrid V-cycle), all through
@@ -646,7 +637,7 @@ def main():
     best = min(results, key=lambda nm: results[nm]["ms"])
     R = results[best]
     t_max = R["ms"]
-    value = world * n / (t_max * 1e-3)
+    value = reps.job_rate(n, t_max)
     info, rec, step_ms = R["info"], R["rec"], R["step_ms"]
     err_exact = float(abs(R["u"] - pr.u_exact[:, 0]).max())
 
@@ -674,7 +665,7 @@ def main():
         if r["amg"]:
             extra = {"amg_levels": r["amg_levels"], "amg_width_max": r["amg_width_max"],
                      "amg_coarse_bytes_per_row": r["amg_coarse"]}
-        return {**extra, "value": world * n / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "iters": r["info"][0],
+        return {**extra, "value": reps.job_rate(n, r["ms"]), "ms_per_step": r["ms"], "iters": r["info"][0],
                 "outer": r["info"][1], "relres": r["info"][2], "status": r["info"][3],
                 "err_exact_inf": float(abs(r["u"] - pr.u_exact[:, 0]).max()),
                 "stage_ms": {"knn": statistics.mean(x[0] for x in r["rec"]),
@@ -739,13 +730,13 @@ def main():
                 e1.record(stream)
             e1.synchronize()
             e_ms.append(e0.elapsed_time(e1))
-        emean = statistics.mean(e_ms)
-        line["e2e"] = {"value": world * n / (emean * 1e-3), "unit": "points/s",
+        emean = max_over_ranks(statistics.mean(e_ms))
+        line["e2e"] = {"value": reps.job_rate(n, emean), "unit": "points/s",
                        "h2d_bytes_per_step": pts_h.numel() * 8 + f_h.numel() * 8,
                        "d2h_bytes_per_step": u_h.numel() * 8, "ms_per_step": emean,
                        "api": "Pipeline.run_host (mvgd_knn, mvgd_assemble, mvgd_solve via ctypes)"}
 
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:  # the oracle on the host: at N = 1 only
         t_setup, t_it, threads = oracle_sample(n, k, solve_iters=40)
         iters_or = oracle_iters_needed()
         if iters_or is not None:
@@ -754,10 +745,9 @@ def main():
                                     "sample": f"full kNN (grid) + assembly of the {n}-point cloud ({t_setup:.2f} s), "
                                               f"40 BiCGSTAB iterations ({t_it * 1e3:.1f} ms each) scaled to the "
                                               f"{iters_or} iterations the oracle needs for 1e-8 on this cloud"}
-    if rank == 0:
+    if reps.leader:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    reps.close()
 
 
 if __name__ == "__main__":
