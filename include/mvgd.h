@@ -261,6 +261,17 @@ mvgd_status mvgd_neumann_ghosts(const double *pts, int64_t n, int32_t k, const i
 size_t mvgd_neumann_fold_workspace_bytes(int64_t nq);
 mvgd_status mvgd_neumann_fold(const mvgd_ell *LQ, const int32_t *q_src, mvgd_ell *LI, void *workspace,
                               size_t workspace_bytes, mvgd_stream_t stream);
+/* mvgd_neumann_rhs: an inhomogeneous condition dU/dn = g (n the boundary's
+ * outward normal in the tangent plane) sets U(ghost) = U(p) + |p - ghost| g(p_b)
+ * (Sec. 3.1).  The known part moves to the right-hand side: the folded system
+ * for (sigma I - L) u = f is (sigma I - L_folded) u = f + c with
+ *   c[i] = sum over the ghost neighbours s of interior row i of w_s |p - ghost_s| g(p_b(s)),
+ * read from Q's operator before the fold (a column whose Q point is >= n_interior
+ * is a ghost).  ghost_dist, ghost_bnd as written by mvgd_neumann_ghosts; g
+ * DEVICE double [n] in the ORIGINAL cloud's point order (read at the boundary
+ * points); c DEVICE double [n_interior] out, interior positions.  Asynchronous. */
+mvgd_status mvgd_neumann_rhs(const mvgd_ell *LQ, int64_t n_interior, const double *ghost_dist,
+                             const int32_t *ghost_bnd, const double *g, double *c, mvgd_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Sets of vectors, for the subspace iteration behind the lowest eigenpairs of

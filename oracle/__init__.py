@@ -22,8 +22,8 @@ the paper they follow):
 * ``normal_matrix``: the 6x6 normal-equation matrix of Sec. 2 as printed.
 * ``system_matrix``, ``gs_eigenvalues``, ``gs_power``: sigma I - L in a given
   row order and the spectrum of its Gauss-Seidel iteration matrix (Sec. 4.1).
-* ``neumann_ghosts``, ``neumann_fold`` (``oracle/neumann.py``): the reflection
-  method for a Neumann boundary (Sec. 3.1).
+* ``neumann_ghosts``, ``neumann_fold``, ``neumann_rhs`` (``oracle/neumann.py``):
+  the reflection method for a Neumann boundary (Sec. 3.1).
 """
 from __future__ import annotations
 
@@ -35,6 +35,7 @@ import numpy as np
 from . import build as _build
 from .neumann import fold as neumann_fold  # noqa: F401
 from .neumann import neumann_ghosts  # noqa: F401
+from .neumann import neumann_rhs  # noqa: F401
 
 DELTA_QUARTER_RANGE = 0
 DELTA_MEAN_NN = 1

@@ -21,6 +21,10 @@ Plain numpy, FP64, in the order the paper takes the steps:
    neighbours are taken in Q, its MVGD row assembled there, and every ghost
    column then points at the interior point it mirrors: with a homogeneous
    condition U(p^R) = U(p), so the weights of a point and of its ghost add up.
+3. An inhomogeneous condition dU/dn = g sets U(p^R) = U(p) + |p - p^R| g(p_b);
+   the known part moves to the right-hand side: row i of L U gains
+   c_i = sum over its ghost neighbours of w_ij |p - p^R| g(p_b), and
+   (sigma I - L) u = f becomes (sigma I - L_folded) u = f + c.
 """
 from __future__ import annotations
 
@@ -116,3 +120,17 @@ def fold(val_q, nbr_q, n_interior: int, q_src) -> tuple:
     (val [n_I][k+1], col [n_I][k]); a column may repeat or equal the row itself."""
     q_src = np.asarray(q_src)
     return np.array(val_q[:n_interior], copy=True), q_src[np.asarray(nbr_q[:n_interior])]
+
+
+def neumann_rhs(val_q, nbr_q, n_interior: int, ghosts: Ghosts, g) -> np.ndarray:
+    """Step 3: c [n_I] for dU/dn = g, g given at every point of the original cloud
+    (read at the boundary points), the outward normal of the boundary."""
+    val_q = np.asarray(val_q, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    c = np.zeros(n_interior)
+    for i in range(n_interior):
+        for s, j in enumerate(nbr_q[i]):
+            if j >= n_interior:
+                t = j - n_interior
+                c[i] += val_q[i, s + 1] * ghosts.dist[t] * g[ghosts.bnd[t]]
+    return c

@@ -30,7 +30,7 @@ EXPORTS = (
     "mvgd_row_signs", "mvgd_dirichlet_rows", "mvgd_block_gram_workspace_bytes", "mvgd_block_gram",
     "mvgd_block_combine", "mvgd_block_zero_rows", "mvgd_gs_power_workspace_bytes", "mvgd_gs_power",
     "mvgd_neumann_ghosts_workspace_bytes", "mvgd_neumann_ghosts", "mvgd_neumann_fold_workspace_bytes",
-    "mvgd_neumann_fold",
+    "mvgd_neumann_fold", "mvgd_neumann_rhs",
 )
 PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
 AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
@@ -172,6 +172,8 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_neumann_fold_workspace_bytes.restype = C.c_size_t
     L.mvgd_neumann_fold.argtypes = [C.POINTER(Ell), _P, C.POINTER(Ell), _P, C.c_size_t, _P]
     L.mvgd_neumann_fold.restype = C.c_int
+    L.mvgd_neumann_rhs.argtypes = [C.POINTER(Ell), C.c_int64, _P, _P, _P, _P, _P]
+    L.mvgd_neumann_rhs.restype = C.c_int
     _lib = L
     return L
 

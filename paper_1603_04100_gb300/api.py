@@ -196,6 +196,7 @@ class NeumannCloud:
     n_ghost: int
     n_boundary: int
     bad_frames: int
+    op_q: "Operator | None" = None  # the operator over interior points and ghosts, before the fold
 
 
 def neumann_ghosts(pts: torch.Tensor, nbr: torch.Tensor, boundary: torch.Tensor, kb: int = 6,
@@ -249,8 +250,24 @@ def neumann_operator(pts: torch.Tensor, boundary: torch.Tensor, k: int, *, kb: i
     if cloud.bad_frames:
         raise LB.MvgdError("mvgd_neumann_ghosts", LB.EDEGENERATE)
     nq, oq = knn(cloud.q, k, want_order=True, stream=stream)
-    op_q = assemble(cloud.q, nq, prec=prec, order=oq, stream=stream)
-    return neumann_fold(op_q, cloud, stream=stream), cloud
+    cloud.op_q = assemble(cloud.q, nq, prec=prec, order=oq, stream=stream)
+    return neumann_fold(cloud.op_q, cloud, stream=stream), cloud
+
+
+def neumann_rhs(cloud: NeumannCloud, g: torch.Tensor, op_q: Operator | None = None, stream=None) -> torch.Tensor:
+    """The term c that dU/dn = g adds to the right-hand side (mvgd_neumann_rhs):
+    solve (sigma I - L_folded) u = f + c.  g: double [n], the original cloud's point
+    order; op_q defaults to the operator neumann_operator assembled over the cloud."""
+    _require_cuda(g, torch.float64, "g")
+    op_q = op_q if op_q is not None else cloud.op_q
+    if op_q is None:
+        raise ValueError("no operator over the cloud: pass op_q")
+    c = torch.empty(cloud.n_interior, dtype=torch.float64, device=g.device)
+    cq = op_q.cstruct()
+    LB.check("mvgd_neumann_rhs", LB.load().mvgd_neumann_rhs(C.byref(cq), cloud.n_interior, _vp(cloud.ghost_dist),
+                                                            _vp(cloud.ghost_bnd), _vp(g), _vp(c),
+                                                            _stream(stream)))
+    return c
 
 
 @dataclass

@@ -214,9 +214,7 @@ MVGD_API mvgd_status mvgd_gs_power(const mvgd_ell* L, double sigma, const double
     if (L->prec == MVGD_FP32_REFINE && !L->val_lo) return MVGD_EINVAL;
     if (!(sigma == sigma) || sigma - sigma != 0.0) return MVGD_EINVAL;
     if (!aligned(L->col) || !aligned(L->val) || !aligned(L->val_lo) || !aligned(ws)) return MVGD_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(x0) & 7) || (reinterpret_cast<uintptr_t>(x) & 7) ||
-        (reinterpret_cast<uintptr_t>(nu) & 7) || (reinterpret_cast<uintptr_t>(status) & 3))
-        return MVGD_EINVAL;
+    if (!aligned(x0) || !aligned(x) || !aligned(nu) || !aligned(status)) return MVGD_EINVAL;
     if (ws_bytes < mvgd_gs_power_workspace_bytes(L->n, iters)) return MVGD_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0, per_sm = 0;

@@ -422,6 +422,29 @@ __global__ void k_fold_rows(mvgd_ell LQ, const int32_t* __restrict__ q_src, cons
     }
 }
 
+// c[p] = sum over the ghost columns s of interior row p of w_s |p - ghost| g(p_b)
+__global__ void k_neumann_rhs(mvgd_ell LQ, int64_t ni, const double* __restrict__ dist,
+                              const int32_t* __restrict__ bnd, const double* __restrict__ g, double* __restrict__ c) {
+    const int k = LQ.k, m = k + 1;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < LQ.n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t qp = LQ.order ? LQ.order[r] : (int32_t)r;
+        if (qp >= ni) continue;
+        double acc = 0.0;
+        for (int s = 0; s < k; s++) {
+            const int32_t cc = LQ.col[sell_index(r, s, k)];
+            const int64_t q2 = LQ.order ? LQ.order[cc] : cc;
+            if (q2 < ni) continue;
+            const int64_t t = q2 - ni;
+            const int64_t e = sell_index(r, s + 1, m);
+            const double w = LQ.prec == MVGD_FP64
+                                 ? static_cast<const double*>(LQ.val)[e]
+                                 : (double)static_cast<const float*>(LQ.val)[e] + (double)LQ.val_lo[e];
+            acc += w * dist[t] * g[bnd[t]];
+        }
+        c[qp] = acc;
+    }
+}
+
 struct FoldLayout {
     size_t keep, newidx, inv, tiles, cnt, total;
 };
@@ -523,5 +546,20 @@ MVGD_API mvgd_status mvgd_neumann_fold(const mvgd_ell* LQ, const int32_t* q_src,
     k_fold_keep<<<g, 256, 0, s>>>(LQ->order, LQ->n, LI->n, keep, inv);
     scan_flags(keep, LQ->n, newidx, tiles, cnt, s);
     k_fold_rows<<<g, 256, 0, s>>>(*LQ, q_src, keep, newidx, inv, *LI);
+    return launch_status();
+}
+
+MVGD_API mvgd_status mvgd_neumann_rhs(const mvgd_ell* LQ, int64_t n_interior, const double* ghost_dist,
+                                      const int32_t* ghost_bnd, const double* g, double* c, mvgd_stream_t stream) {
+    if (!LQ || !ghost_dist || !ghost_bnd || !g || !c || !LQ->col || !LQ->val) return MVGD_EINVAL;
+    if (LQ->n < 1 || LQ->n >= (1ll << 31) || n_interior < 1 || n_interior > LQ->n || LQ->k < kMinK ||
+        LQ->k > kMaxK)
+        return MVGD_EINVAL;
+    if (LQ->prec != MVGD_FP64 && LQ->prec != MVGD_FP32_REFINE) return MVGD_EINVAL;
+    if (LQ->prec == MVGD_FP32_REFINE && !LQ->val_lo) return MVGD_EINVAL;
+    if (!aligned(ghost_dist) || !aligned(ghost_bnd) || !aligned(g) || !aligned(c) || !aligned(LQ->col) ||
+        !aligned(LQ->val) || !aligned(LQ->val_lo) || !aligned(LQ->order))
+        return MVGD_EINVAL;
+    k_neumann_rhs<<<grid_for(LQ->n), 256, 0, (cudaStream_t)stream>>>(*LQ, n_interior, ghost_dist, ghost_bnd, g, c);
     return launch_status();
 }

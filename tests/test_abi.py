@@ -115,6 +115,11 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
     ei = LB.Ell(100, 10, LB.FP64, None, C.c_void_p(1024), C.c_void_p(2048), None)
     assert L.mvgd_neumann_fold(C.byref(eq), C.c_void_p(768), C.byref(ei), C.c_void_p(8192), 1 << 20,
                                None) == LB.EINVAL
+    # the condition's term: more interior points than rows, a misaligned output
+    assert L.mvgd_neumann_rhs(C.byref(eq), 121, C.c_void_p(256), C.c_void_p(512), C.c_void_p(768),
+                              C.c_void_p(1024), None) == LB.EINVAL
+    assert L.mvgd_neumann_rhs(C.byref(eq), 100, C.c_void_p(256), C.c_void_p(512), C.c_void_p(768),
+                              C.c_void_p(1032), None) == LB.EINVAL
     e4 = LB.Ell(100, 4, LB.FP64, None, C.c_void_p(256), C.c_void_p(512), None)
     assert L.mvgd_row_signs(C.byref(e4), C.c_void_p(256), None) == LB.EINVAL  # k < 5
     assert L.mvgd_spmv(C.byref(e), LB.SPMV_F32, 1, 1.0, 1.0, C.c_void_p(256), 0.0, C.c_void_p(512),

@@ -93,6 +93,53 @@ def test_folded_rows_sum_to_zero():
     assert np.any(col == np.arange(val.shape[0])[:, None])
 
 
+def test_inhomogeneous_condition_is_exact_for_quadratic_data_on_a_plane():
+    # half-disk y >= 0 with the rim on y = 0: the outward normal is -y, so for
+    # u = 3y + y^2 - x^2 / 2 the condition is g = -du/dy = -3 on the rim, and the
+    # ghost values U(p) + 2 y g = -3y + y^2 - x^2 / 2 are u's own values there: the
+    # extended data is one quadratic, which the MVGD rows differentiate exactly
+    p, b = _half_disk(3000, 60, 1)
+    R, t = _rotation(2), np.array([0.3, -1.2, 2.0])
+    pm = p @ R.T + t
+    nbr = oracle.knn_grid(pm, 16)
+    g = oracle.neumann_ghosts(pm, b, nbr)
+    q, q_src = g.cloud(pm)
+    nq = oracle.knn_grid(q, 16)
+    vq, st, _, _ = oracle.assemble(q, nq)
+    n_i = g.interior.size
+    val, col = oracle.neumann_fold(vq, nq, n_i, q_src)
+    x, y = p[g.interior, 0], p[g.interior, 1]
+    u = 3.0 * y + y * y - 0.5 * x * x
+    c = oracle.neumann_rhs(vq, nq, n_i, g, np.full(pm.shape[0], -3.0))
+    lap = oracle.to_csr(val, col) @ u + c          # L applied to the extended data
+    scale = np.abs(val).sum(1) * np.abs(u).max()
+    assert np.all(np.abs(lap - 1.0) <= 1e-10 * scale), np.abs(lap - 1.0).max()
+    # without the condition's term the rows near the rim are wrong
+    assert np.abs(oracle.to_csr(val, col) @ u - 1.0).max() > 1.0
+
+
+def test_inhomogeneous_hemisphere_converges_to_the_exact_solution():
+    # u = z on the upper hemisphere: the rim's outward normal in the tangent plane is
+    # -z, so dU/dn = -1; -Delta z = 2 z, so (I - L) u = 3 z with the condition's term
+    import scipy.sparse.linalg as spl
+    errs = []
+    for n in (4000, 16000):
+        p, b = I.hemisphere(n, 3)
+        nbr = oracle.knn_grid(p, 20)
+        g = oracle.neumann_ghosts(p, b, nbr)
+        q, q_src = g.cloud(p)
+        nq = oracle.knn_grid(q, 20)
+        vq, _, _, _ = oracle.assemble(q, nq)
+        val, col = oracle.neumann_fold(vq, nq, g.interior.size, q_src)
+        z = p[g.interior, 2]
+        A = oracle.system_matrix(val, col, 1.0).tocsc()
+        c = oracle.neumann_rhs(vq, nq, g.interior.size, g, np.full(n, -1.0))
+        errs.append(np.abs(spl.spsolve(A, 3.0 * z + c) - z).max())
+        if n == 4000:  # without the term the rim condition is dU/dn = 0: far from z
+            assert np.abs(spl.spsolve(A, 3.0 * z) - z).max() > 0.5
+    assert errs[0] < 0.01 and errs[1] < errs[0] / 3, errs
+
+
 def test_neumann_hemisphere_spectrum():
     want = np.array([0.0, 2, 2, 6, 6, 6, 12, 12, 12, 12, 20, 20, 20, 20, 20])
     errs = []
