@@ -2,9 +2,10 @@
 
 The exact spectrum is lambda_n = n (n + 1) with multiplicity 2n + 1; the
 paper prints the MVGD errors E^2_n, E^inf_n of lambda_4 = 20 and lambda_8 = 72
-on random samplings of 2000-16000 points (tests/golden/eigen_errors_sec4_3.txt).
-Our random samples are not the paper's, so its numbers pin the size and the
-decay of the error, not its digits.
+on random and uniform samplings of 2000-16000 points
+(tests/golden/eigen_errors_sec4_3.txt).  Our random samples are not the
+paper's, so its numbers pin the size and the decay of the error, not its
+digits; the uniform rows are taken on the Fibonacci lattice.
 """
 from __future__ import annotations
 
@@ -50,19 +51,31 @@ def test_constants_are_the_zero_mode():
     assert np.all(np.abs(lam[1:4] - 2.0) <= 0.05)  # the l = 1 triple
 
 
-def test_random_sphere_errors_match_the_printed_table():
+def _table(sampling, points):
     g = _golden()
-    e2, einf = [], []
+    ours = {f"{sampling}_{m}_lambda{l}": [] for m in ("E2", "Einf") for l in (4, 8)}
     for n_pts in g["samples"]:
-        lam = _eigs(int(n_pts), 1)
-        a, b = oracle.multiplet_errors(lam, 4)
-        e2.append(100 * a)
-        einf.append(100 * b)
-    for ours, paper in ((e2, g["random_E2_lambda4"]), (einf, g["random_Einf_lambda4"])):
-        ratio = np.array(ours) / np.array(paper)
-        assert np.all((ratio > 0.4) & (ratio < 2.5)), (ours, paper)
-    # the error falls with the sampling density (about second order in h)
-    assert e2[-1] < e2[0] / 4 and einf[-1] < einf[0] / 4
+        p = points(int(n_pts))
+        nbr = oracle.knn_grid(p, 20)
+        val, st, _, _ = oracle.assemble(p, nbr)
+        assert int(st.max()) == 0
+        lam = oracle.lb_eigenvalues(val, nbr, 81)  # lambda_8 = 72 is eigenvalues 64 .. 80
+        for l in (4, 8):
+            a, b = oracle.multiplet_errors(lam, l)
+            ours[f"{sampling}_E2_lambda{l}"].append(100 * a)
+            ours[f"{sampling}_Einf_lambda{l}"].append(100 * b)
+    return g, ours
+
+
+@pytest.mark.parametrize("sampling", ["random", "uniform"])
+def test_sphere_errors_match_the_printed_table(sampling):
+    points = (lambda n: I.random_sphere(n, 1)) if sampling == "random" else I.fibonacci_sphere
+    g, ours = _table(sampling, points)
+    for key, vals in ours.items():
+        ratio = np.array(vals) / np.array(g[key])
+        assert np.all((ratio > 0.4) & (ratio < 3.0)), (key, vals, g[key])
+        # the error falls with the sampling density (about second order in h)
+        assert vals[-1] < vals[0] / 4, (key, vals)
 
 
 def test_dirichlet_hemisphere_spectrum():
