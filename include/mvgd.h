@@ -278,7 +278,7 @@ mvgd_status mvgd_neumann_rhs(const mvgd_ell *LQ, int64_t n_interior, const doubl
  * the LB operator (Sec. 4.3).  A set of p vectors of length n (FP64, DEVICE,
  * 256-byte aligned) is stored in blocks of w interleaved columns (1 <= w <= 8),
  * each block a right-hand-side array [n][w] of mvgd_solve / mvgd_spmv:
- *   element (r, c) at (c / w) * n * w + r * w + (c % w);  p, q multiples of w, <= 64.
+ *   element (r, c) at (c / w) * n * w + r * w + (c % w);  p, q multiples of w, <= 128.
  * mvgd_block_gram: G = X^T Y (p x q, row-major, DEVICE) summed in a fixed
  *   order (256 row ranges, each in row order, then the ranges in order), so the
  *   result does not depend on the GPU; ws sized by mvgd_block_gram_workspace_bytes.

@@ -15,8 +15,8 @@ namespace mvgd {
 namespace {
 
 constexpr int kGramBlocks = 256;  // row ranges of the first reduction stage
-constexpr int kGramRows = 32;     // rows staged in shared memory at a time
-constexpr int kMaxCols = 64;      // p, q <= kMaxCols
+constexpr int kGramRows = 16;     // rows staged in shared memory at a time
+constexpr int kMaxCols = 128;     // p, q <= kMaxCols
 
 __device__ __forceinline__ int64_t at(int64_t r, int c, int64_t n, int w) {
     return (int64_t)(c / w) * n * w + r * w + (c % w);
@@ -66,18 +66,16 @@ __global__ void k_gram_final(const double* __restrict__ partial, int outs, doubl
     }
 }
 
-// Y(r, j) = sum_i X(r, i) C[i][j]   (C row-major p x q, staged in shared memory)
+// Y(r, j) = sum_i X(r, i) C[i][j]   (C row-major p x q, at most 128 KB: read
+// through the read-only cache, where the threads of a block share it)
 __global__ void __launch_bounds__(256) k_block_combine(const double* __restrict__ X, int p,
                                                        const double* __restrict__ Cm, int q, int64_t n, int w,
                                                        double* __restrict__ Y) {
-    __shared__ double cs[kMaxCols * kMaxCols];
-    for (int e = threadIdx.x; e < p * q; e += blockDim.x) cs[e] = Cm[e];
-    __syncthreads();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * q; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = e / q;
         const int j = (int)(e % q);
         double s = 0.0;
-        for (int i = 0; i < p; i++) s = fma(X[at(r, i, n, w)], cs[i * q + j], s);
+        for (int i = 0; i < p; i++) s = fma(X[at(r, i, n, w)], __ldg(Cm + i * q + j), s);
         Y[at(r, j, n, w)] = s;
     }
 }

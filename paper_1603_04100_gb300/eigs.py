@@ -9,7 +9,7 @@ Shift-invert subspace iteration on A = sigma I - L, whose smallest eigenvalues
   H = X^T (L X)        mvgd_spmv with sigma = 0, alpha = -1 per block, then a Gram;
 and the Ritz values of the p x p matrix H estimate the eigenvalues of L
 (lambda = -theta).  Every O(n) step runs in the library's kernels; only the
-p x p Cholesky factor and the Ritz values of H (p <= 64) are computed on the
+p x p Cholesky factor and the Ritz values of H (p <= 128) are computed on the
 host, as in reverse-communication eigensolvers.  The operator is not
 symmetric, so H is not either; its eigenvalues near a multiplet of the
 sphere come out real up to rounding, and their real parts are reported.
@@ -97,8 +97,8 @@ def lowest_eigenpairs(op: api.Operator, nev: int, *, extra: int = 8, sigma: floa
     right-hand side there returns zero up to its tolerance; the rows are re-zeroed
     after each solve, since A^-1 amplifies them by 1 / sigma against 1 / (sigma + lambda))."""
     p = ((nev + extra + W - 1) // W) * W
-    if p > 64:
-        raise ValueError("nev + extra must be at most 64")
+    if p > 128:
+        raise ValueError("nev + extra must be at most 128")
     dev = op.col.device
     st = stream if stream is not None else torch.cuda.current_stream(dev)
     mask = None

@@ -14,7 +14,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,p,q,w", [(1000, 8, 8, 8), (4097, 24, 16, 8), (70001, 40, 40, 8), (33, 6, 3, 3)])
+@pytest.mark.parametrize("n,p,q,w", [(1000, 8, 8, 8), (4097, 24, 16, 8), (70001, 40, 40, 8), (33, 6, 3, 3),
+                                     (5003, 128, 96, 8)])
 def test_block_gram_and_combine(n, p, q, w):
     dev = cuda_or_skip()
     from paper_1603_04100_gb300 import _lib as LB
@@ -67,6 +68,25 @@ def test_lowest_eigenvalues_match_oracle(prec_name):
     assert abs(res.values[0]) <= 1e-8
     e2, _ = oracle.multiplet_errors(res.values, 4)
     assert e2 <= 0.02
+
+
+def test_lambda8_multiplet_matches_oracle():
+    # the 81 lowest eigenvalues (through lambda_8 = 72, eigenvalues 64 .. 80): a basis of 96 vectors
+    dev = cuda_or_skip()
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300.eigs import lowest_eigenpairs
+    p = I.random_sphere(4000, 1)
+    pt = torch.from_numpy(p).to(dev)
+    nbr_t, ord_t = api.knn(pt, 20, want_order=True)
+    op = api.assemble(pt, nbr_t, prec=api.FP64, order=ord_t)
+    res = lowest_eigenpairs(op, 81, maxit=400)
+    assert res.vectors.shape[0] * res.vectors.shape[2] == 96
+    assert res.change <= 1e-8, (res.iterations, res.change)
+    val, _, _, _ = oracle.assemble(p, nbr_t.cpu().numpy())
+    want = oracle.lb_eigenvalues(val, nbr_t.cpu().numpy(), 81)
+    assert np.all(np.abs(res.values - want) <= 1e-6 * np.maximum(want, 1.0)), np.abs(res.values - want).max()
+    e2, einf = oracle.multiplet_errors(res.values, 8)
+    assert e2 <= 0.05 and einf <= 0.08
 
 
 def test_dirichlet_hemisphere_eigenvalues_match_oracle():
