@@ -84,7 +84,10 @@ mvgd_status mvgd_knn(const double *pts, int64_t n, int32_t k, int32_t *nbr, int3
  * looks up the array's device address (set-up, once per device), so make it
  * before any stream capture.  All calls on a device share the array: calls
  * whose work may overlap on the GPU (unordered streams) race on it and must be
- * serialised by the caller.  Results are identical to mvgd_knn. */
+ * serialised by the caller.  Results are identical to mvgd_knn.  The looked-up
+ * address is cached per device for the life of the process; after
+ * cudaDeviceReset the cache is stale, so do not call this entry point again in
+ * a process that has reset a device it used. */
 #define MVGD_KNN_NOALLOC_MAX_POINTS 65536
 mvgd_status mvgd_knn_noalloc(const double *pts, int64_t n, int32_t k, int32_t *nbr, int32_t *order,
                              double cell_size, mvgd_stream_t stream);
@@ -506,6 +509,31 @@ mvgd_status mvgd_request_poll(void *const *reqs, int32_t count, int32_t *done, m
  * ------------------------------------------------------------------------ */
 mvgd_status mvgd_trace_enable(int32_t on);
 int32_t mvgd_trace_read(uint64_t *out, int32_t max);
+
+/* ------------------------------------------------------------------------
+ * Bounded device-side waits (liveness; the paper has no counterpart).  The
+ * persistent kernels wait on one another: the grid barriers of the solver
+ * (mvgd_solve, mvgd_iterate) and of mvgd_gs_power, and the row flags of
+ * mvgd_gs_power's forward substitution.  Every such wait polls at most a
+ * limited number of times; a wait that runs out sets MVGD_ETIMEOUT, every
+ * other block of the launch then stops at its next wait, the launch ends, and
+ * the status reaches the caller through mvgd_solve_info / the status word.
+ * The context stays usable and the next call on the same workspace runs
+ * normally (each launch resets its barrier and flags).
+ * mvgd_set_wait_limit: polls a wait may take before it gives up, for launches
+ *   made from now on, process-wide (a poll is one L2 round trip, about
+ *   0.5-1 us).  0 restores each kernel's default (seconds: never reached by
+ *   co-resident blocks that make progress).  MVGD_EINVAL if polls < 0.
+ * mvgd_test_withhold_arrival: a test control for those paths.  on != 0 arms
+ *   it for exactly one launch: in the next solver launch block 0 leaves its
+ *   arrival at the first grid barrier out, and in the next mvgd_gs_power
+ *   launch row 0's flag of the first step is never published.  Nothing else
+ *   ends those waits, so they run out at the limit and the launch returns
+ *   MVGD_ETIMEOUT; no memory is touched that a normal launch would not touch.
+ *   on == 0 disarms it.  Host-side only; returns MVGD_OK.
+ * ------------------------------------------------------------------------ */
+mvgd_status mvgd_set_wait_limit(int64_t polls);
+mvgd_status mvgd_test_withhold_arrival(int32_t on);
 
 #ifdef __cplusplus
 }

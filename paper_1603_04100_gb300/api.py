@@ -471,6 +471,18 @@ def operator_from_rows(nbr: np.ndarray, val: np.ndarray, prec: int = FP64, devic
 STEP_NAMES = {0: "PRE_A", 1: "A", 2: "PRE_B", 3: "B", 4: "C"}
 
 
+def set_wait_limit(polls: int = 0) -> None:
+    """Polls a device-side wait may take before it ends its launch with
+    MVGD_ETIMEOUT (mvgd_set_wait_limit); 0 restores the kernels' defaults."""
+    LB.check("mvgd_set_wait_limit", LB.load().mvgd_set_wait_limit(int(polls)))
+
+
+def withhold_arrival(on: bool = True) -> None:
+    """Arm (or disarm) the one-launch test control mvgd_test_withhold_arrival: the
+    next solver or Gauss-Seidel launch has one wait that nothing ends."""
+    LB.check("mvgd_test_withhold_arrival", LB.load().mvgd_test_withhold_arrival(1 if on else 0))
+
+
 def trace_enable(on: bool = True) -> None:
     """Turn the solver's step trace on (clearing it) or off."""
     LB.check("mvgd_trace_enable", LB.load().mvgd_trace_enable(1 if on else 0))

@@ -1,5 +1,21 @@
-// Status strings and version of the C ABI.
+// Status strings, version and the bounded-wait controls of the C ABI.
+#include <atomic>
+
 #include "common.cuh"
+
+namespace mvgd {
+namespace {
+std::atomic<long long> g_wait_limit{0};  // 0: each kernel's own default
+std::atomic<int> g_withhold{0};
+}  // namespace
+
+long long wait_limit_or(long long dflt) {
+    const long long v = g_wait_limit.load();
+    return v > 0 ? v : dflt;
+}
+
+bool take_withhold() { return g_withhold.exchange(0) != 0; }
+}  // namespace mvgd
 
 MVGD_API const char* mvgd_status_string(mvgd_status s) {
     switch (s) {
@@ -18,3 +34,14 @@ MVGD_API const char* mvgd_status_string(mvgd_status s) {
 }
 
 MVGD_API int32_t mvgd_version(void) { return 100; }
+
+MVGD_API mvgd_status mvgd_set_wait_limit(int64_t polls) {
+    if (polls < 0) return MVGD_EINVAL;
+    mvgd::g_wait_limit.store((long long)polls);
+    return MVGD_OK;
+}
+
+MVGD_API mvgd_status mvgd_test_withhold_arrival(int32_t on) {
+    mvgd::g_withhold.store(on ? 1 : 0);
+    return MVGD_OK;
+}

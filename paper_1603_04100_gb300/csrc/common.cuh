@@ -49,6 +49,12 @@ inline mvgd_status launch_status() {
     return cudaGetLastError() == cudaSuccess ? MVGD_OK : MVGD_ECUDA;
 }
 
+// Host side of mvgd_set_wait_limit / mvgd_test_withhold_arrival (capi.cu):
+// the poll limit a launch made now should use (dflt unless the caller set
+// one), and the one-shot withhold control (true once after it was armed).
+long long wait_limit_or(long long dflt);
+bool take_withhold();
+
 // ---------------------------------------------------------------------------
 // Warp helpers
 // ---------------------------------------------------------------------------
@@ -146,13 +152,16 @@ __device__ __forceinline__ void red_release_add_gpu(unsigned* p, unsigned v) {
 // atomic followed by a released generation word: about 1 us less per barrier
 // for 456 blocks on GB300.  `epoch` is the caller's count of barriers passed,
 // the same in every block.
-__device__ __forceinline__ bool grid_sync(GridBarrier b, unsigned& epoch, int* err, long long limit) {
+// `arrive` false (only the withhold test control passes it) leaves this block's
+// arrival out, so the barrier cannot complete and every block's wait runs out.
+__device__ __forceinline__ bool grid_sync(GridBarrier b, unsigned& epoch, int* err, long long limit,
+                                          bool arrive = true) {
     __syncthreads();
     bool ok = true;
     epoch += 1u;
     if (threadIdx.x == 0) {
         const unsigned target = epoch * gridDim.x;
-        red_release_add_gpu(b.count, 1u);
+        if (arrive) red_release_add_gpu(b.count, 1u);
         long long polls = 0;
         while ((int)(ld_acquire_gpu(b.count) - target) < 0) {
             if ((++polls & 255) == 0 && (polls > limit || *(volatile int*)err != 0)) {

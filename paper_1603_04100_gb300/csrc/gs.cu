@@ -41,6 +41,9 @@ struct GsArgs {
     double* part;     // [grid]
     unsigned* bar;    // barrier counter
     int* err;
+    long long poll_limit;     // polls of one row flag before MVGD_ETIMEOUT
+    long long barrier_limit;  // polls of the grid barrier
+    int withhold;             // test control: row 0's first flag is never published
 };
 
 __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
@@ -104,7 +107,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_power(GsArgs a) {
     __syncthreads();
     double s0 = range_sumsq(a.buf0, 1.0, r0, r1, red);
     if (threadIdx.x == 0) a.part[blockIdx.x] = s0;
-    if (!grid_sync(bar, epoch, a.err, kGsBarrierLimit)) goto done;
+    if (!grid_sync(bar, epoch, a.err, a.barrier_limit)) goto done;
     {
         double tot = grid_total(a.part, &total);
         if (!(tot > 0.0) || !isfinite(tot)) {
@@ -133,7 +136,7 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_power(GsArgs a) {
                     } else {
                         long long polls = 0;
                         while (ld_acquire_gpu(a.flag + j) != done_mark) {
-                            if ((++polls & 255) == 0 && (polls > kGsPollLimit || *(volatile int*)a.err != 0)) {
+                            if ((++polls & 255) == 0 && (polls > a.poll_limit || *(volatile int*)a.err != 0)) {
                                 atomicCAS(a.err, 0, (int)MVGD_ETIMEOUT);
                                 break;
                             }
@@ -147,14 +150,14 @@ __global__ void __launch_bounds__(kGsThreads) k_gs_power(GsArgs a) {
                 if (lane == 0) {
                     const double d = a.sigma - weight(val, lo_w, sell_index(r, 0, m)) + dself;
                     __stcg(dst + r, (up - lo) / d);
-                    st_release_gpu(a.flag + r, done_mark);
+                    if (!(a.withhold && it == 0 && r == 0)) st_release_gpu(a.flag + r, done_mark);
                 }
                 if (*(volatile int*)a.err != 0) break;
             }
-            if (!grid_sync(bar, epoch, a.err, kGsBarrierLimit)) goto done;
+            if (!grid_sync(bar, epoch, a.err, a.barrier_limit)) goto done;
             const double sb = range_sumsq(dst, 1.0, r0, r1, red);
             if (threadIdx.x == 0) a.part[blockIdx.x] = sb;
-            if (!grid_sync(bar, epoch, a.err, kGsBarrierLimit)) goto done;
+            if (!grid_sync(bar, epoch, a.err, a.barrier_limit)) goto done;
             tot = grid_total(a.part, &total);
             const double nrm = sqrt(tot);
             if (blockIdx.x == 0 && threadIdx.x == 0) a.nu[it] = nrm;
@@ -243,6 +246,9 @@ MVGD_API mvgd_status mvgd_gs_power(const mvgd_ell* L, double sigma, const double
     a.part = reinterpret_cast<double*>(base + lay.part);
     a.bar = reinterpret_cast<unsigned*>(base + lay.ctl);
     a.err = reinterpret_cast<int*>(base + lay.ctl) + 1;
+    a.poll_limit = wait_limit_or(kGsPollLimit);
+    a.barrier_limit = wait_limit_or(kGsBarrierLimit);
+    a.withhold = take_withhold() ? 1 : 0;
     // flags, tickets and the control words start at zero; the flag and ticket
     // regions are contiguous
     MVGD_CUDA_TRY(cudaMemsetAsync(base + lay.flag, 0, lay.part - lay.flag, s));

@@ -108,6 +108,7 @@ struct Ctl {
     const int* cancel;
     long long limit;
     int trace;       // record each step's end time (mvgd_trace_enable)
+    int withhold;    // test control: block 0 leaves its first barrier arrival out
 };
 
 // ------------------------------------------------------------------------------
@@ -234,6 +235,7 @@ struct Stager {
 
     __device__ void issue(int b, const int32_t* colsrc, const void* valsrc, int esize, int k, int64_t slice) {
         __syncwarp();  // every lane has consumed what buffer b held
+        if (!ok) return;  // after a missed wait the warp issues nothing more
         busy |= 1u << b;
         if (lane_id() == 0) {
             const uint32_t cb = (uint32_t)(kSlice * k * 4), vb = (uint32_t)(kSlice * (k + 1) * esize);
@@ -269,17 +271,24 @@ struct Stager {
         return b;
     }
 
-    // Warp-collective bounded wait for buffer b.
+    // Warp-collective bounded wait for buffer b.  A copy that missed its wait
+    // stays marked busy with its parity unchanged, so drain() waits for it
+    // again before the block's shared memory is released.
     __device__ bool wait(int b, int* err) {
-        const bool landed = mbar_wait(&bar[b], (parity >> b) & 1u, kStageWaitLimit);
-        parity ^= 1u << b;
-        busy &= ~(1u << b);
-        ok = __all_sync(0xffffffffu, landed) && ok;
-        if (!ok && lane_id() == 0) atomicCAS(err, 0, (int)MVGD_ETIMEOUT);
+        if (!ok) return false;  // nothing was issued since the first miss
+        const bool landed = __all_sync(0xffffffffu, mbar_wait(&bar[b], (parity >> b) & 1u, kStageWaitLimit));
+        if (landed) {
+            parity ^= 1u << b;
+            busy &= ~(1u << b);
+        } else {
+            ok = false;
+            if (lane_id() == 0) atomicCAS(err, 0, (int)MVGD_ETIMEOUT);
+        }
         return ok;
     }
 
-    // Before the block's shared memory goes away: bounded waits for copies in flight.
+    // Before the block's shared memory goes away: bounded waits for every copy
+    // still in flight (landed or not, each buffer's wait ends within its limit).
     __device__ void drain() {
         for (int b = 0; b < 2; b++)
             if (busy & (1u << b)) mbar_wait(&bar[b], (parity >> b) & 1u, kStageWaitLimit);
@@ -956,7 +965,8 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
             *ctl.stop = 1;
         if (reduce) held = -1;  // the states were advanced at the arrivals
-        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit);
+        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit,
+                                  !(ctl.withhold && blockIdx.x == 0 && bar_epoch == 0));
         trace_step(ctl, (unsigned)ph);
         return ok;
     };
@@ -1088,7 +1098,8 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 }
             }
         }
-        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit);
+        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit,
+                                  !(ctl.withhold && blockIdx.x == 0 && bar_epoch == 0));
         trace_step(ctl, 0x1000u | ((unsigned)side << 8) | ((unsigned)kind << 4) | (unsigned)l);
         return ok;
     };
@@ -1586,8 +1597,9 @@ MVGD_API mvgd_status mvgd_iterate(const mvgd_request* reqs, int32_t count, int32
     ctl.nrestart = C.words + 2;
     ctl.stop = C.words + 3;
     ctl.cancel = cancel;
-    ctl.limit = 20000000ll;  // polls of >= 32 ns each: seconds, never reached by co-resident blocks
+    ctl.limit = wait_limit_or(20000000ll);  // polls of >= 32 ns each: seconds, never reached by co-resident blocks
     ctl.trace = g_trace_on;
+    ctl.withhold = take_withhold() ? 1 : 0;
     mvgd_status st;
     if (prec == MVGD_FP32_REFINE)
         st = amg ? dispatch_q<true, true>(maxQ, tab, ctl, max_iterations, kmax, s)

@@ -85,10 +85,10 @@ def hemisphere(n: int, seed: int, nb: int | None = None) -> tuple[np.ndarray, np
     return pts, boundary
 
 
-def morton_sorted(pts: np.ndarray, bits: int = 10) -> np.ndarray:
-    """The same points reordered along a Z-order curve of their bounding cube
-    (`bits` per axis, stable in the original index): consecutive points are
-    then spatial neighbours, as in the stored order the kNN step produces."""
+def morton_permutation(pts: np.ndarray, bits: int = 10) -> np.ndarray:
+    """Indices that order the points along a Z-order curve of their bounding
+    cube (`bits` per axis, stable in the original index): consecutive points
+    are then spatial neighbours, as in the stored order the kNN step produces."""
     lo = pts.min(axis=0)
     span = float((pts.max(axis=0) - lo).max()) or 1.0
     q = np.minimum(((pts - lo) / span * (1 << bits)).astype(np.int64), (1 << bits) - 1)
@@ -96,7 +96,12 @@ def morton_sorted(pts: np.ndarray, bits: int = 10) -> np.ndarray:
     for b in range(bits):
         for d in range(3):
             code |= ((q[:, d] >> b) & 1) << (3 * b + d)
-    return np.ascontiguousarray(pts[np.argsort(code, kind="stable")])
+    return np.argsort(code, kind="stable")
+
+
+def morton_sorted(pts: np.ndarray, bits: int = 10) -> np.ndarray:
+    """The same points reordered along a Z-order curve (morton_permutation)."""
+    return np.ascontiguousarray(pts[morton_permutation(pts, bits)])
 
 
 def ellipsoid(n: int, seed: int, axes=(1.0, 0.7, 0.4)) -> np.ndarray:

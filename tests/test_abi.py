@@ -146,3 +146,14 @@ def test_binding_modules_import():
     import importlib
     for mod in ("api", "batch", "eigs", "pipeline", "serve", "inputs", "profile_case"):
         importlib.import_module(f"paper_1603_04100_gb300.{mod}")
+
+
+def test_wait_limit_controls_are_host_side(lib_path):
+    # both controls only set host state read by the next launch: callable without a GPU
+    from paper_1603_04100_gb300 import _lib as LB
+    L = LB.load(lib_path)
+    assert L.mvgd_set_wait_limit(-1) == LB.EINVAL
+    assert L.mvgd_set_wait_limit(4096) == LB.OK
+    assert L.mvgd_set_wait_limit(0) == LB.OK
+    assert L.mvgd_test_withhold_arrival(1) == LB.OK
+    assert L.mvgd_test_withhold_arrival(0) == LB.OK

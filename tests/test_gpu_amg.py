@@ -13,6 +13,7 @@ import oracle
 from oracle import amg as OA
 from paper_1603_04100_gb300 import inputs as I
 from tests.gpu_util import cuda_or_skip
+from tests.oracle_util import backward_ok, reference_solution, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -121,19 +122,21 @@ def test_multigrid_preconditioned_solve(prec_name):
     _, nbr, val, f = _solve_case(n, 20, 34)
     op = api.operator_from_rows(nbr, val, prec, dev)
     ft = torch.from_numpy(f).to(dev)
-    plain = api.solve(op, ft, rtol=1e-9, precond=1)
-    res = api.solve(op, ft, rtol=1e-9, precond=2)
-    assert res.status == [0], res.status
-    assert res.relres[0] <= 1e-9
     # several times fewer Krylov iterations than the row-scaled solve
-    assert 4 * res.iters[0] < plain.iters[0], (res.iters, plain.iters)
+    plain = api.solve(op, ft, rtol=1e-9, precond=1)
+    res9 = api.solve(op, ft, rtol=1e-9, precond=2)
+    assert res9.status == [0], res9.status
+    assert 4 * res9.iters[0] < plain.iters[0], (res9.iters, plain.iters)
+    # parity: a tight solve against the oracle's (FP64 multigrid BiCGSTAB with refinement)
+    res = api.solve(op, ft, rtol=1e-11, precond=2)
+    assert res.status == [0] and res.relres[0] <= 1e-11, (res.status, res.relres)
     u = res.u.cpu().numpy()
-    # backward error with the oracle's own FP64 operator
-    r = f - oracle.spmv(val, nbr, u, sigma=1.0)
-    assert np.linalg.norm(r) <= 1.05e-9 * np.linalg.norm(f)
-    u_or, _, rel_or, st = oracle.bicgstab(val, nbr, f, 1.0, rtol=1e-11)  # the plain oracle stalls near 1e-12 here
-    assert st == 0 and rel_or <= 1e-11
-    assert np.linalg.norm(u - u_or) / np.linalg.norm(u_or) <= 1e-7
+    assert backward_ok(val, nbr, u, f, 1e-11)
+    u_or, _, rel_or = OA.solve_refined(OA.hierarchy(val, nbr, 1.0), f, rtol=1e-11)
+    assert rel_or <= 1e-11
+    assert rel_l2(u, u_or) <= 1e-8, rel_l2(u, u_or)
+    # the 1e-9 solve is within 1e-8 of the oracle too
+    assert rel_l2(res9.u.cpu().numpy(), u_or) <= 1e-8, rel_l2(res9.u.cpu().numpy(), u_or)
 
 
 def test_multigrid_solve_of_a_single_level_system_is_direct():
@@ -167,6 +170,34 @@ def test_multigrid_batch_equals_solo():
             assert torch.equal(solo.slots[0].u, both.slots[i].u), (prec, i)
             info = api.decode_info(both.slots[i].info)
             assert all(st == 0 and rel <= 1e-8 for _, _, rel, st in info), info
+
+
+def test_multigrid_batch_matches_oracle():
+    # every cloud of one batched launch (FP32 inner + FP64 refinement, multigrid)
+    # against the oracle's own kNN, rows and tight solve of that cloud
+    dev = cuda_or_skip()
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300.batch import BatchPipeline
+    sizes = [(9000, 12, 2), (30000, 20, 1), (450, 16, 1), (20000, 16, 3)]
+    clouds = [I.random_sphere(sizes[0][0], 40), I.ellipsoid(sizes[1][0], 41), I.random_sphere(sizes[2][0], 42),
+              I.torus(sizes[3][0], 43)]
+    fs = [np.stack([c[:, 0], c[:, 1] * c[:, 2], np.sin(c[:, 0]) * np.exp(c[:, 1])][:q], axis=1).copy()
+          for c, (_, _, q) in zip(clouds, sizes)]
+    bp = BatchPipeline(sizes, prec=api.FP32_REFINE, precond=2, device=dev, rtol=1e-11)
+    bp.run([torch.from_numpy(c).to(dev) for c in clouds], [torch.from_numpy(x).to(dev) for x in fs])
+    torch.cuda.synchronize()
+    for i, (n, k, q) in enumerate(sizes):
+        info = api.decode_info(bp.slots[i].info)
+        assert all(st == 0 and rel <= 1e-11 for _, _, rel, st in info), (i, info)
+        nbr = oracle.knn_grid(clouds[i], k)
+        assert np.array_equal(bp.slots[i].nbr.cpu().numpy(), nbr)
+        val, st, _, _ = oracle.assemble(clouds[i], nbr)
+        assert int(st.max()) == 0
+        u_or, _, rels = reference_solution(clouds[i], nbr, val, fs[i], rtol=1e-11)
+        assert max(rels) <= 1e-11
+        u = bp.slots[i].u.cpu().numpy()
+        for c in range(q):
+            assert rel_l2(u[:, c], u_or[:, c]) <= 1e-8, (i, c, rel_l2(u[:, c], u_or[:, c]))
 
 
 def _zorder_keys(pts):

@@ -138,11 +138,11 @@ def test_neumann_solve_end_to_end(prec_name, precond):
                                      prec=getattr(api, prec_name))
     assert np.array_equal(cloud.interior.cpu().numpy(), g.interior)
     x = p[g.interior, 0]
-    res = api.solve(op, torch.from_numpy(3.0 * x).to(dev), rtol=1e-9, precond=precond)
+    res = api.solve(op, torch.from_numpy(3.0 * x).to(dev), rtol=1e-11, precond=precond)
     assert res.status == [0], res.status
     u = res.u.cpu().numpy()
     u_or = _sparse_solve(val, col, 3.0 * x)
-    assert np.linalg.norm(u - u_or) / np.linalg.norm(u_or) <= 1e-7
+    assert np.linalg.norm(u - u_or) / np.linalg.norm(u_or) <= 1e-8
     assert abs(np.abs(u - x).max() - np.abs(u_or - x).max()) <= 1e-6
     assert np.abs(u - x).max() <= 2e-2
 
@@ -162,10 +162,10 @@ def test_inhomogeneous_solve_end_to_end():
         op, cloud = api.neumann_operator(torch.from_numpy(p).to(dev), torch.from_numpy(b).to(dev), 20,
                                          prec=api.FP32_REFINE)
         c = api.neumann_rhs(cloud, torch.from_numpy(gv).to(dev))
-        res = api.solve(op, torch.from_numpy(3.0 * z).to(dev) + c, rtol=1e-10, precond=2)
+        res = api.solve(op, torch.from_numpy(3.0 * z).to(dev) + c, rtol=1e-11, precond=2)
         assert res.status == [0], res.status
         u = res.u.cpu().numpy()
-        assert np.linalg.norm(u - u_or) / np.linalg.norm(u_or) <= 1e-7
+        assert np.linalg.norm(u - u_or) / np.linalg.norm(u_or) <= 1e-8
         errs.append(np.abs(u - z).max())
     # the condition's term makes u = z the discrete solution's limit: the error falls
     assert errs[0] < 0.05 and errs[1] < errs[0] / 2, errs

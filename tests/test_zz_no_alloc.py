@@ -41,11 +41,11 @@ def test_noalloc_knn_equals_knn_on_consecutive_calls():
     clouds = [(I.torus(5000, 3), 16), (I.random_sphere(MAX_POINTS, 4), 20), (I.torus(5000, 3), 16)]
     for pts_np, k in clouds:  # back to back: each call inherits the previous call's scratch contents
         pts = torch.from_numpy(pts_np).to(dev)
-        want = api.knn(pts, k)
+        want, want_order = api.knn(pts, k, want_order=True)
         st, nbr, order = _noalloc(L, pts, k)
         assert st == LB.OK, LB.status_string(st)
         assert torch.equal(nbr, want)
-        assert torch.equal(torch.sort(order.long()).values, torch.arange(pts.shape[0], device=dev))
+        assert torch.equal(order, want_order)  # the exported row order too, element for element
 
 
 def test_noalloc_knn_refuses_clouds_above_its_maximum():
