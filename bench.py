@@ -42,7 +42,8 @@ RTOL = 1e-8
 # launch of the current kernel read 21.513 GB and wrote 0.645 GB.  Valid for this
 # kernel and workload only; any other path or size reports traffic null.
 KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = (21.513e9 + 0.645e9) / 20
-BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see run_batched)
+BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see batched_measure)
+SERVED_REQUESTS, SERVED_RATE = 60, 20.0  # the served slice in the default line (below saturation)
 WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
             "6 nearest, u = 5z^3-3z, f = 13u, (I-L)u = f to 1e-8 relative residual")
 
@@ -64,6 +65,11 @@ def parse():
     ap.add_argument("--paths", default="fp32_refine+amg,fp64+amg,fp32_refine,fp64",
                     help="comma list of <precision>[+amg] paths to time (the fastest is the headline)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched / served / open-surface / eigenvalue lines after the headline")
+    ap.add_argument("--profile-case", type=int, nargs=4, metavar=("N", "PREC", "ITERS", "PRECOND"),
+                    help="profiling target only: kNN + assembly + a solve capped at ITERS iterations on an "
+                         "N-point random sphere, PREC 0 FP64 / 1 FP32+refine, PRECOND 1 row scaling / 2 multigrid")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -376,26 +382,66 @@ def amg_coarse_bytes(H, n: int) -> float:
 ORACLE_ITERS_FILE = ROOT / "oracle" / "iterations_random_sphere_1m_k20.json"
 
 
-def oracle_sample(n: int, k: int, solve_iters: int = 40):
-    """kNN + assembly of the full cloud and `solve_iters` BiCGSTAB iterations of
-    the oracle; returns (seconds for knn+assembly, seconds per iteration, threads)."""
-    import oracle
-    from paper_1603_04100_gb300 import inputs as I
-    threads = oracle.threads(os.cpu_count() or 1)
-    pr = I.random_sphere_problem(n, k, seed=SEED)
-    t0 = time.perf_counter()
-    nbr = oracle.knn_grid(pr.pts, k)
-    val, _, _, _ = oracle.assemble(pr.pts, nbr, delta_m=6)
-    t1 = time.perf_counter()
-    oracle.bicgstab(val, nbr, pr.f[:, 0], rtol=1e-30, maxit=solve_iters)
-    t2 = time.perf_counter()
-    return t1 - t0, (t2 - t1) / (solve_iters + 2), threads
+REF_SAMPLE_ITERS = 4  # preconditioned oracle iterations timed per reference step
 
 
-def oracle_iters_needed() -> int | None:
-    if ORACLE_ITERS_FILE.exists():
-        return int(json.loads(ORACLE_ITERS_FILE.read_text())["iters"])
-    return None
+class OracleSampler:
+    """Bounded samples of the workload on the FP64 oracle, on the host cores.
+
+    Once: the oracle's kNN and rows of the full cloud and its multigrid
+    hierarchy (oracle/amg.py, rows relabelled along a Z-order curve), timed.
+    Each sample() then times the oracle's kNN (grid) and assembly of the full
+    cloud again and REF_SAMPLE_ITERS iterations of its multigrid-preconditioned
+    BiCGSTAB.  The full solve is projected from the recorded iteration count of
+    that same solver on this workload (ORACLE_ITERS_FILE, written by
+    oracle/measure_iterations.py): setup + hierarchy + iterations x time per
+    iteration."""
+
+    def __init__(self, n: int, k: int):
+        import oracle
+        from oracle import amg as OA
+        from paper_1603_04100_gb300 import inputs as I
+        self.oracle, self.OA = oracle, OA
+        self.n, self.k = n, k
+        self.threads = oracle.threads(os.cpu_count() or 1)
+        self.pr = I.random_sphere_problem(n, k, seed=SEED)
+        self.perm = I.morton_permutation(self.pr.pts)
+        self.inv = np.empty_like(self.perm)
+        self.inv[self.perm] = np.arange(n)
+        nbr = oracle.knn_grid(self.pr.pts, k)
+        val, _, _, _ = oracle.assemble(self.pr.pts, nbr, delta_m=6)
+        t0 = time.perf_counter()
+        self.levels = OA.hierarchy(val[self.perm], self.inv[nbr[self.perm]].astype(np.int32), 1.0)
+        self.hierarchy_s = time.perf_counter() - t0
+        self.f = np.ascontiguousarray(self.pr.f[self.perm, 0])
+        rec = json.loads(ORACLE_ITERS_FILE.read_text()) if ORACLE_ITERS_FILE.exists() else {}
+        self.iters_needed = int(rec["multigrid"]["iters"]) if "multigrid" in rec else None
+        self.iters_plain = int(rec["bicgstab"]["iters"]) if "bicgstab" in rec else None
+
+    def sample(self) -> dict:
+        t0 = time.perf_counter()
+        nbr = self.oracle.knn_grid(self.pr.pts, self.k)
+        self.oracle.assemble(self.pr.pts, nbr, delta_m=6)
+        t1 = time.perf_counter()
+        self.OA.bicgstab_right(self.levels, self.f, rtol=1e-30, maxit=REF_SAMPLE_ITERS)
+        t2 = time.perf_counter()
+        return {"setup_s": t1 - t0, "iteration_s": (t2 - t1) / REF_SAMPLE_ITERS, "sample_s": t2 - t0}
+
+    def summarise(self, samples) -> dict:
+        setup = statistics.median(x["setup_s"] for x in samples)
+        it = statistics.median(x["iteration_s"] for x in samples)
+        full = setup + self.hierarchy_s + it * self.iters_needed
+        return {"value": self.n / full, "unit": "points/s", "cores": self.threads, "kind": "oracle",
+                "sample_ms": statistics.median(x["sample_s"] for x in samples) * 1e3,
+                "projected_full_solve_ms": full * 1e3,
+                "projection": f"kNN + assembly ({setup:.2f} s, timed each step) + multigrid hierarchy "
+                              f"({self.hierarchy_s:.2f} s, timed once) + {self.iters_needed} iterations x "
+                              f"{it * 1e3:.0f} ms (the iteration count of this oracle solver to 1e-8 on this "
+                              f"cloud, {ORACLE_ITERS_FILE.name})",
+                "sample": f"the oracle (C kNN and assembly with {self.threads} OpenMP threads, numpy multigrid "
+                          f"BiCGSTAB) on the full {self.n}-point cloud: kNN + assembly + {REF_SAMPLE_ITERS} "
+                          f"preconditioned iterations a step",
+                "unpreconditioned_oracle_iters": self.iters_plain}
 
 
 def run_reference(args):
@@ -403,29 +449,29 @@ def run_reference(args):
     if rank != 0:
         return
     n, k = args.n, args.k
-    iters = oracle_iters_needed()
-    if iters is None:
+    if not ORACLE_ITERS_FILE.exists() or "multigrid" not in json.loads(ORACLE_ITERS_FILE.read_text()):
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration count file missing"}))
         return
+    t_begin = time.perf_counter()
+    samp = OracleSampler(n, k)
     samples = []
     for s in range(args.warmup + args.steps):
-        t_setup, t_it, threads = oracle_sample(n, k, solve_iters=20 if s < args.warmup else 40)
+        x = samp.sample()
         if s >= args.warmup:
-            samples.append((t_setup, t_it))
-    t_setup = statistics.median(x[0] for x in samples)
-    t_it = statistics.median(x[1] for x in samples)
-    total = t_setup + t_it * iters
-    value = n / total
+            samples.append(x)
+    base = samp.summarise(samples)
+    value = base["value"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["sample_ms"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "k": k, "rtol": RTOL, "parallelism": "host cores"},
-        "cpu_baseline": {"value": value, "unit": "points/s", "cores": threads, "kind": "oracle",
-                         "sample": f"full kNN (grid) + assembly of the {n}-point cloud, then 40 BiCGSTAB "
-                                   f"iterations timed and scaled to the {iters} iterations the oracle needs "
-                                   f"for 1e-8 on this cloud ({ORACLE_ITERS_FILE.name})"},
+        "projected_full_solve_ms": base["projected_full_solve_ms"],
+        "value_basis": "value = points / projected_full_solve_ms; ms_per_step is the bounded sample each step "
+                       "actually timed",
+        "cpu_baseline": base,
         "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": time.perf_counter() - t_begin,
     }
     print(json.dumps(line), flush=True)
 
@@ -433,46 +479,31 @@ def run_reference(args):
 # ------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------
-def run_batched(args):
-    """256 uneven clouds (2k-262k points, sphere / ellipsoid / torus, K 12 or 20, 4 RHS) as one batch:
-    kNN per cloud on a stream pool, one batched assembly, one multigrid set-up per cloud, one persistent
-    solver launch for all; points/s over the whole batch, against the same clouds solved one at a time
-    by the plain FP64 path (row scaling).
-
-    With K = 12 on uniformly random points about 0.1 % of the MVGD rows have a non-positive diagonal
-    and many of those systems do not reach 1e-8 in any solver at hand (the FP64 oracle's own BiCGSTAB,
-    GMRES(50) and multigrid-BiCGSTAB included), so every arm stops at BATCH_MAXIT iterations and the
-    line reports how many clouds (and points) converged."""
+def batched_measure(dev, reps, specs, steps: int, warmup: int, arms=(("fp32_refine+amg", 1, 2), ("fp64+amg", 0, 2)),
+                    workload: str = ""):
+    """Uneven clouds as one batch: kNN per cloud on a stream pool, one batched assembly, one
+    multigrid set-up per cloud, one persistent solver launch for all; points/s over the batch,
+    against the same clouds solved one at a time by the plain FP64 path (row scaling).  Every
+    arm stops at BATCH_MAXIT iterations a cloud and reports the clouds and points that converged."""
     import torch
-    from paper_1603_04100_gb300 import api, build
-    from paper_1603_04100_gb300 import inputs as I
+    from paper_1603_04100_gb300 import api
     from paper_1603_04100_gb300.batch import BatchPipeline
     from paper_1603_04100_gb300.pipeline import Pipeline
-    from paper_1603_04100_gb300.replicas import Replicas
-    build.build()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    reps = Replicas("nccl", dev)  # N GPUs: N replicas of the batch, timed by the slowest
-    specs = I.batched_specs(256, seed=2)
     probs = [sp.build() for sp in specs]
     pts = [torch.from_numpy(p.pts).to(dev) for p in probs]
     fs = [torch.from_numpy(np.ascontiguousarray(p.f)).to(dev) for p in probs]
     sizes = [(p.pts.shape[0], p.k, p.f.shape[1]) for p in probs]
     total = sum(s[0] for s in sizes)
-    out = {"metric": "MVGD points/s, 256-cloud batch (assembly+solve to 1e-8 rel)", "unit": "points/s",
-           "n_gpus": reps.world, "scaling": "weak", "data": "synthetic", "config": {"workload": "batched: 256 clouds, N log-uniform 2,000-262,144 "
-           "(seed 2), sphere/ellipsoid/torus, K in {12, 20}, 4 RHS (x, yz, x^2-y^2, sin x e^y)", "points": total,
-           "maxit": BATCH_MAXIT,
-           "rhs": sum(s[2] for s in sizes)}, "paths": {}}
-    for name, prec, precond in (("fp32_refine+amg", api.FP32_REFINE, 2), ("fp64+amg", api.FP64, 2)):
+    out = {"config": {"workload": workload, "clouds": len(sizes), "points": total, "maxit": BATCH_MAXIT,
+                      "rhs": sum(s[2] for s in sizes)}, "paths": {}}
+    for name, prec, precond in arms:
         bp = BatchPipeline(sizes, prec=prec, precond=precond, device=dev, maxit=BATCH_MAXIT,
                            inner_maxit=BATCH_MAXIT)
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             bp.run(pts, fs)
         reps.barrier()
         ms = []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, steps)):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             bp.run(pts, fs)
@@ -491,7 +522,7 @@ def run_batched(args):
                               "mean_iters": statistics.mean(iters),
                               "converged_clouds": sum(conv), "converged_points": sum(
                                   s[0] for s, c in zip(sizes, conv) if c),
-                              "converged_k20": sum(c for s, c in zip(sizes, conv) if s[1] == 20)}
+                              "gpu_launches": bp.kernels_per_run}
         del bp
         torch.cuda.empty_cache()
     # plain: the same clouds one at a time, FP64 with row scaling
@@ -518,38 +549,27 @@ def run_batched(args):
     out["value"] = out["paths"][best]["value"]
     out["path"] = best
     out["vs_plain"] = out["value"] / out["paths"]["plain_fp64_one_by_one"]["value"]
-    if reps.leader:
-        print(json.dumps(out))
-    reps.close()
+    return out
 
 
-def run_served(args):
-    """The first --requests requests of the Poisson trace (200/s, 1k-1M points, 1-8 RHS) through the
-    serving loop (HBM-budget admission, continuous batching in epochs of the persistent solver)."""
+def served_measure(dev, reps, count: int, rate: float, arms):
+    """The first `count` requests of the Poisson trace (seed 3) re-timed at `rate` requests/s
+    through the serving loop (HBM-budget admission, continuous batching in epochs of the
+    persistent solver).  An arm is (name, precision, preconditioner, max requests at once):
+    max 1 is the plain per-request path, each request alone."""
     import torch
-    from paper_1603_04100_gb300 import api, build
     from paper_1603_04100_gb300 import inputs as I
-    from paper_1603_04100_gb300.replicas import Replicas
     from paper_1603_04100_gb300.serve import Server, requests_from_trace
-    build.build()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = f"cuda:{local}"
-    reps = Replicas("nccl", torch.device(dev))  # N GPUs: N servers, each on its own copy of the trace
-    trace = I.serving_trace(count=args.requests, seed=3, rate_per_s=args.rate)
-    out = {"metric": "MVGD served points/s and latency (assembly+solve to 1e-8 rel)", "unit": "points/s",
-           "n_gpus": reps.world, "scaling": "weak", "data": "synthetic",
-           "config": {"workload": f"served: first {args.requests} requests of the Poisson trace (seed 3) at "
-                                  f"{args.rate:g}/s, N log-uniform 1,000-1,048,576, K 20, 1-8 RHS, 120 GB budget"},
-           "paths": {}}
-    for name, prec, precond in (("fp32_refine+amg", api.FP32_REFINE, 2), ("fp64+amg", api.FP64, 2)):
+    trace = I.serving_trace(count=count, seed=3, rate_per_s=rate)
+    out = {"config": {"workload": f"served: first {count} requests of the Poisson trace (seed 3) at {rate:g}/s, "
+                                  f"N log-uniform 1,000-1,048,576, K 20, 1-8 RHS, 120 GB budget"}, "paths": {}}
+    for name, prec, precond, max_active in arms:
         reqs = requests_from_trace(trace)
-        srv = Server(dev, prec=prec, precond=precond, hbm_budget=120e9)
         warm = requests_from_trace(trace[:2])
         for r in warm:
             r.arrival_s = 0.0
-        srv.serve(warm, realtime=False)
-        srv = Server(dev, prec=prec, precond=precond, hbm_budget=120e9)
+        Server(dev, prec=prec, precond=precond, hbm_budget=120e9, max_active=max_active).serve(warm, realtime=False)
+        srv = Server(dev, prec=prec, precond=precond, hbm_budget=120e9, max_active=max_active)
         reps.barrier()
         stats = srv.serve(reqs, realtime=True)
         reps.barrier()
@@ -560,6 +580,42 @@ def run_served(args):
         stats["p99_ms"] = reps.max(stats["p99_ms"])
         out["paths"][name] = stats
         torch.cuda.empty_cache()
+    return out
+
+
+def _gpu_setup():
+    import torch
+    from paper_1603_04100_gb300 import build
+    from paper_1603_04100_gb300.replicas import Replicas
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    return dev, Replicas("nccl", dev)
+
+
+def run_batched(args):
+    """256 uneven clouds (2k-262k points, sphere / ellipsoid / torus, K 12 or 20, 4 RHS)."""
+    from paper_1603_04100_gb300 import inputs as I
+    dev, reps = _gpu_setup()  # N GPUs: N replicas of the batch, timed by the slowest
+    out = {"metric": "MVGD points/s, 256-cloud batch (assembly+solve to 1e-8 rel)", "unit": "points/s",
+           "n_gpus": reps.world, "scaling": "weak", "data": "synthetic"}
+    out.update(batched_measure(dev, reps, I.batched_specs(256, seed=2), args.steps, args.warmup,
+                               workload="batched: 256 clouds, N log-uniform 2,000-262,144 (seed 2), "
+                                        "sphere/ellipsoid/torus, K in {12, 20}, 4 RHS (x, yz, x^2-y^2, sin x e^y)"))
+    if reps.leader:
+        print(json.dumps(out))
+    reps.close()
+
+
+def run_served(args):
+    """The first --requests requests of the Poisson trace through the serving loop."""
+    from paper_1603_04100_gb300 import api
+    dev, reps = _gpu_setup()  # N GPUs: N servers, each on its own copy of the trace
+    out = {"metric": "MVGD served points/s and latency (assembly+solve to 1e-8 rel)", "unit": "points/s",
+           "n_gpus": reps.world, "scaling": "weak", "data": "synthetic"}
+    out.update(served_measure(dev, reps, args.requests, args.rate,
+                              (("fp32_refine+amg", api.FP32_REFINE, 2, 1024), ("fp64+amg", api.FP64, 2, 1024))))
     best = max(out["paths"], key=lambda k: out["paths"][k]["points_per_s"])
     out["value"] = out["paths"][best]["points_per_s"]
     out["p50_ms"] = out["paths"][best]["p50_ms"]
@@ -570,8 +626,34 @@ def run_served(args):
     reps.close()
 
 
+def run_profile_case(n: int, prec: int, iters: int, precond: int):
+    """A profiling target (Nsight Compute): kNN + assembly + a solve capped at `iters`
+    iterations on a random unit sphere of n points (K = 20), run twice."""
+    import torch
+    from paper_1603_04100_gb300 import api, build
+    from paper_1603_04100_gb300 import inputs as I
+    build.build()
+    dev = torch.device("cuda:0")
+    pr = I.random_sphere_problem(n, 20, seed=0)
+    pts = torch.from_numpy(pr.pts).to(dev)
+    f = torch.from_numpy(pr.f).to(dev)
+    for _ in range(2):
+        nbr, order = api.knn(pts, 20, want_order=True)
+        op = api.assemble(pts, nbr, prec=prec, order=order)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record()
+        r = api.solve(op, f, rtol=1e-8, precond=precond, maxit=iters)
+        t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    print("ok", r.iters, r.outer, "solve %.3f ms, %.1f us per iteration" % (ms, 1e3 * ms / max(1, r.iters[0])))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(*args.profile_case)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -730,10 +812,27 @@ def main():
     # (FP32 difference form on hi weights, FP64 standard form), L2 flushed before each launch
     line["spmv"] = spmv_roofline(results, n, k, flush, stream, peak, peak_kind)
     line["row_signs"] = row_sign_stats(pts, mixed, k, flush, stream)
-    line["dirichlet_hemisphere"] = dirichlet_hemisphere(n, k, flush, stream)
-    line["neumann_hemisphere"] = neumann_hemisphere(n, k, flush, stream)
-    line["lb_eigenvalues"] = lb_eigen_stats(k, stream)
-    line["gauss_seidel_spectral_radius"] = gs_spectral_stats(k, stream)
+    if not args.no_extras:
+        line["dirichlet_hemisphere"] = dirichlet_hemisphere(n, k, flush, stream)
+        line["neumann_hemisphere"] = neumann_hemisphere(n, k, flush, stream)
+        line["lb_eigenvalues"] = lb_eigen_stats(k, stream)
+        line["gauss_seidel_spectral_radius"] = gs_spectral_stats(k, stream)
+        from paper_1603_04100_gb300 import inputs as I
+        # the batched workload's K = 20 clouds (all of them converge to 1e-8; the K = 12 ones are
+        # reported by --workload batched), one batch against the plain path one cloud at a time
+        line["batched_k20"] = batched_measure(
+            dev, reps, [sp for sp in I.batched_specs(256, seed=2) if sp.k == 20], 2, 1,
+            arms=(("fp32_refine+amg", api.FP32_REFINE, 2),),
+            workload="the K = 20 clouds of the batched workload (256 clouds, seed 2): sphere/ellipsoid/torus, "
+                     "N log-uniform 2,000-262,144, 4 RHS")
+        # the serving loop below saturation: continuous batching against the plain
+        # per-request FP64 path (one request at a time, row scaling)
+        line["served"] = served_measure(dev, reps, SERVED_REQUESTS, SERVED_RATE,
+                                        (("fp32_refine+amg", api.FP32_REFINE, 2, 1024),
+                                         ("plain_fp64_per_request", api.FP64, 1, 1)))
+        sv = line["served"]["paths"]
+        line["served"]["vs_plain_points_per_s"] = (sv["fp32_refine+amg"]["points_per_s"]
+                                                   / sv["plain_fp64_per_request"]["points_per_s"])
 
     if not args.no_e2e:
         pts_h = torch.from_numpy(pr.pts).pin_memory()
@@ -760,14 +859,9 @@ def main():
                        "api": "Pipeline.run_host (mvgd_knn, mvgd_assemble, mvgd_solve via ctypes)"}
 
     if rank == 0 and world == 1 and not args.no_cpu:  # the oracle on the host: at N = 1 only
-        t_setup, t_it, threads = oracle_sample(n, k, solve_iters=40)
-        iters_or = oracle_iters_needed()
-        if iters_or is not None:
-            total = t_setup + t_it * iters_or
-            line["cpu_baseline"] = {"value": n / total, "unit": "points/s", "cores": threads, "kind": "oracle",
-                                    "sample": f"full kNN (grid) + assembly of the {n}-point cloud ({t_setup:.2f} s), "
-                                              f"40 BiCGSTAB iterations ({t_it * 1e3:.1f} ms each) scaled to the "
-                                              f"{iters_or} iterations the oracle needs for 1e-8 on this cloud"}
+        if ORACLE_ITERS_FILE.exists() and "multigrid" in json.loads(ORACLE_ITERS_FILE.read_text()):
+            samp = OracleSampler(n, k)
+            line["cpu_baseline"] = samp.summarise([samp.sample()])
     if reps.leader:
         print(json.dumps(line), flush=True)
     reps.close()

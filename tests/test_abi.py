@@ -144,7 +144,7 @@ def test_argument_errors_are_reported_before_any_launch(lib_path):
 def test_binding_modules_import():
     # the Python layer imports without a GPU (the CUDA path is only reached on a call)
     import importlib
-    for mod in ("api", "batch", "eigs", "pipeline", "serve", "inputs", "profile_case"):
+    for mod in ("api", "batch", "eigs", "pipeline", "serve", "inputs", "replicas"):
         importlib.import_module(f"paper_1603_04100_gb300.{mod}")
 
 

@@ -65,7 +65,7 @@ def _run_pipeline(pr, prec, rtol):
     return pipe
 
 
-def _check_pipeline(name, prec_name, rtol):
+def _check_pipeline(name, prec_name, rtol, fwd_bar=1e-8):
     from paper_1603_04100_gb300 import api
     pr, nbr, val, u_or = _oracle_case(name)
     pipe = _run_pipeline(pr, getattr(api, prec_name), rtol)
@@ -82,7 +82,7 @@ def _check_pipeline(name, prec_name, rtol):
     fwd = rel_l2(u, u_or)
     print(f"[{name} {prec_name} rtol={rtol:g}] iters={iters} outer={outer} relres={relres:.3e} "
           f"forward={fwd:.3e} weights={err.max():.3e}")
-    assert fwd <= 1e-8, fwd
+    assert fwd <= fwd_bar, (fwd, fwd_bar)
     # the discretisation error against the exact solution is the oracle's, to three digits
     e_gpu = np.abs(u - pr.u_exact[:, 0]).max()
     e_or = np.abs(u_or - pr.u_exact[:, 0]).max()
@@ -98,7 +98,15 @@ def test_sphere_1m_matches_oracle(prec_name, rtol):
 
 @pytest.mark.parametrize("k", [16, 24])
 def test_torus_524k_matches_oracle(k):
-    _check_pipeline(f"torus_k{k}", "FP32_REFINE", 1e-8)
+    # here f = u - Delta u is about 35 u (|Delta u| ~ (4/r^2 + 9/rho^2) |u|), so a 1e-8
+    # residual bounds the forward error only by about rtol ||f|| / ||u|| (A = I - L has
+    # no eigenvalue below 1 on smooth modes); the 1e-8 forward bar is checked on a
+    # solve to 1e-10
+    pr, _, _, u_or = _oracle_case(f"torus_k{k}")
+    amplification = np.linalg.norm(pr.f[:, 0]) / np.linalg.norm(u_or)
+    assert 20 < amplification < 60, amplification
+    _check_pipeline(f"torus_k{k}", "FP32_REFINE", 1e-8, fwd_bar=1e-8 * amplification)
+    _check_pipeline(f"torus_k{k}", "FP32_REFINE", 1e-10, fwd_bar=1e-8)
 
 
 def _check_hierarchy(H, levels):
