@@ -38,10 +38,9 @@ METRIC = "MVGD points/s (assembly+solve to 1e-8 rel) batched/served vs plain; p5
 N_DEFAULT, K_DEFAULT, SEED = 1_048_576, 20, 0
 RTOL = 1e-8
 # DRAM bytes (read + write) per iteration of k_solve<1,1,1> on the bench workload
-# (N = 1,048,576, K = 20, multigrid, FP32 inner): an ncu capture of a 20-iteration
-# launch of the current kernel read 21.513 GB and wrote 0.645 GB.  Valid for this
-# kernel and workload only; any other path or size reports traffic null.
-KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = (21.513e9 + 0.645e9) / 20
+# (N = 1,048,576, K = 20, multigrid, FP32 inner), from an ncu capture of the
+# current kernel; None until one is taken (the line then reports traffic null).
+KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = None
 BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see batched_measure)
 SERVED_REQUESTS, SERVED_RATE = 60, 20.0  # the served slice in the default line (below saturation)
 WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
@@ -362,7 +361,7 @@ def gs_spectral_stats(k, stream, n_pts: int = 16000, iters: int = 300):
 def amg_coarse_bytes(H, n: int) -> float:
     """Bytes per fine row that one V-cycle moves on levels >= 1: per level, down
     and up read each stored entry (int32 column + FP32 value) once, plus about
-    36 bytes of vectors per row; the coarsest solve reads its dense FP32 inverse."""
+    36 bytes of vectors per row; the coarsest solve reads its dense FP64 inverse."""
     total = 0.0
     for lv in range(1, H.levels):
         cnt = H.level_rows(lv)[0] if lv < H.levels - 1 else None
@@ -372,7 +371,7 @@ def amg_coarse_bytes(H, n: int) -> float:
         else:
             total += 4.0 * info.n * info.n + 8.0 * info.n
     if H.levels == 1:
-        total += 4.0 * n * n
+        total += 8.0 * n * n
     return total / n
 
 
@@ -755,7 +754,8 @@ def main():
     achieved = bytes_solve / (solve_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (KSOLVE_MIXED_AMG_DRAM_PER_ITERATION * info[0]
-                            if best == "fp32_refine+amg" and n == N_DEFAULT and k == K_DEFAULT else None),
+                            if KSOLVE_MIXED_AMG_DRAM_PER_ITERATION is not None and best == "fp32_refine+amg"
+                            and n == N_DEFAULT and k == K_DEFAULT else None),
                 "traffic_note": "ncu DRAM bytes per iteration of the same kernel on this workload x the launch's "
                                 "iterations; below the algorithmic bytes because the Krylov vectors stay in L2",
                 "kernel": "k_solve (persistent BiCGSTAB, " + ("FP32 inner + FP64 refinement" if mixed_best else "FP64")

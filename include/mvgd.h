@@ -113,7 +113,8 @@ typedef struct {
     int32_t m;        /* MEAN_NN only */
     double scale;     /* 1.0 = the paper's rule */
     int32_t variant;  /* mvgd_row_variant; 0 (zero-initialised) = MVGD */
-    int32_t reserved; /* 0 */
+    int32_t arith;    /* 0: the arithmetic of the storage format (below); 1: FP64
+                         arithmetic for MVGD_FP32_REFINE too */
 } mvgd_delta_rule;
 
 /* Which row the assembly forms.  MVGD_ROW_MVGD is the method (Sec. 3.1).
@@ -129,6 +130,20 @@ typedef enum {
     MVGD_FP32_REFINE = 1  /* weights as FP32 hi + FP32 lo (hi + lo = the FP64 weight to
                              ~2^-48 relative); FP32 inner Krylov on hi, FP64 residual on hi+lo */
 } mvgd_precision;
+
+/* Arithmetic of the assembly.  MVGD_FP64 rows are formed in FP64 (the local
+ * fit by Householder QR).  MVGD_FP32_REFINE rows are formed on the FP32 pipe
+ * unless rule.arith == 1: offsets p_j - p_i in FP64, then covariance and
+ * h-scaled local coordinates in double-float (pairs of FP32 numbers, about 48
+ * bits), the 3x3 eigenvectors
+ * from an FP32 Jacobi polished by FP64 Jacobi sweeps, and the least-squares
+ * fits through normal equations solved with an FP32 Cholesky factor and
+ * refined from double-float residuals (for k >= 8: a fit over fewer points is
+ * square or nearly so and always uses FP64); the hi + lo weights then agree with the
+ * FP64 arithmetic's to about cond(V)^2 2^-48 (cond(V) of the h-scaled design
+ * matrix, typically below 100).  A row whose factor is nearly singular or whose
+ * refinement does not settle is formed in FP64 instead, so row_status and the
+ * rank test are those of the FP64 arithmetic. */
 
 /* Sparse operator in sliced ELL form, slice height 32.  Row r (0 <= r < n)
  * of the stored matrix is point order[r] (order == NULL: point r).  Element
@@ -159,9 +174,10 @@ size_t mvgd_ell_bytes(int64_t n, int32_t k, int32_t prec, int32_t which);
  * h-scaled coordinates), 2 = non-finite value; bad_rows (optional out, one
  * device int32, zeroed by this call) counts the rows with status != 0.
  * Asynchronous: check row_status / bad_rows after the stream has run.
- * The workspace (size from mvgd_assemble_workspace_bytes) is needed only when
- * L->order is set; it holds the inverse order that maps neighbour indices to
- * stored rows. */
+ * The workspace (size from mvgd_assemble_workspace_bytes) is needed when
+ * L->order is set (the inverse order that maps neighbour indices to stored
+ * rows) or when the rows are formed on the FP32 pipe (the list of rows
+ * handed to the FP64 arithmetic). */
 size_t mvgd_assemble_workspace_bytes(int64_t n);
 mvgd_status mvgd_assemble(const double *pts, int64_t n, int32_t k, const int32_t *nbr,
                           mvgd_delta_rule rule, mvgd_ell *L, double *h, uint8_t *row_status,
@@ -293,6 +309,20 @@ mvgd_status mvgd_block_gram(const double *X, int32_t p, const double *Y, int32_t
                             double *G, void *ws, size_t ws_bytes, mvgd_stream_t stream);
 mvgd_status mvgd_block_combine(const double *X, int32_t p, const double *C, int32_t q, int64_t n, int32_t w,
                                double *Y, mvgd_stream_t stream);
+/* Host-side p x p steps of the same eigensolver (HOST pointers, row-major,
+ * synchronous, p <= 128; the paper's eigs does the same on the projected
+ * matrices of its Arnoldi process):
+ * mvgd_block_chol_inverse: Rinv = R^-1 for the upper-triangular Cholesky factor
+ *   R^T R = (G + G^T) / 2 of a Gram matrix G (the orthonormalisation
+ *   X = Y R^-1).  MVGD_EDEGENERATE if G is not positive definite.
+ * mvgd_ritz_values: the p eigenvalues (re[i] + i im[i], complex pairs adjacent)
+ *   of a general real matrix H -- the Ritz values of the projected operator
+ *   X^T L X -- by Householder reduction to Hessenberg form and Francis
+ *   double-shift QR (Golub and Van Loan, Algorithms 7.4.2, 7.5.1-7.5.2).
+ *   MVGD_ENONFINITE for a non-finite entry, MVGD_ENOCONV if a block does not
+ *   deflate within 60 p steps. */
+mvgd_status mvgd_block_chol_inverse(const double *G, int32_t p, double *Rinv);
+mvgd_status mvgd_ritz_values(const double *H, int32_t p, double *re, double *im);
 /* mvgd_block_zero_rows: X(r, c) = 0 for all c at the rows r with mask[r] != 0
  * (DEVICE uint8 [n], the set's row order); keeps a subspace off Dirichlet rows. */
 mvgd_status mvgd_block_zero_rows(double *X, int32_t p, int64_t n, int32_t w, const uint8_t *mask,
@@ -364,7 +394,8 @@ typedef struct {
     double rtol;         /* relative residual target, e.g. 1e-8 */
     int32_t maxit;       /* cap on Krylov iterations (inner ones included) */
     int32_t inner_maxit; /* FP32_REFINE: cap per inner solve */
-    double inner_rtol;   /* FP32_REFINE: inner relative tolerance, e.g. 1e-5 */
+    double inner_rtol;   /* FP32_REFINE: inner relative tolerance, e.g. 1e-3 (with the multigrid
+                            preconditioner fewer Krylov iterations in all than 1e-4 or 1e-5) */
     int32_t max_outer;   /* FP32_REFINE: cap on refinement steps */
     int32_t precond;     /* 0 = none; 1 = left scaling of each row of the Krylov system by
                             1 / (|sigma| + sum_s |w_s|) (row equilibration: always positive,

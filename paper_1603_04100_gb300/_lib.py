@@ -31,6 +31,7 @@ EXPORTS = (
     "mvgd_block_combine", "mvgd_block_zero_rows", "mvgd_gs_power_workspace_bytes", "mvgd_gs_power",
     "mvgd_neumann_ghosts_workspace_bytes", "mvgd_neumann_ghosts", "mvgd_neumann_fold_workspace_bytes",
     "mvgd_neumann_fold", "mvgd_neumann_rhs", "mvgd_set_wait_limit", "mvgd_test_withhold_arrival",
+    "mvgd_block_chol_inverse", "mvgd_ritz_values",
 )
 PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
 AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
@@ -38,7 +39,7 @@ AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.
 
 class DeltaRule(C.Structure):
     _fields_ = [("kind", C.c_int32), ("m", C.c_int32), ("scale", C.c_double), ("variant", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("arith", C.c_int32)]
 
 
 class Ell(C.Structure):
@@ -174,6 +175,10 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_neumann_fold.restype = C.c_int
     L.mvgd_neumann_rhs.argtypes = [C.POINTER(Ell), C.c_int64, _P, _P, _P, _P, _P]
     L.mvgd_neumann_rhs.restype = C.c_int
+    L.mvgd_block_chol_inverse.argtypes = [_P, C.c_int32, _P]
+    L.mvgd_block_chol_inverse.restype = C.c_int
+    L.mvgd_ritz_values.argtypes = [_P, C.c_int32, _P, _P]
+    L.mvgd_ritz_values.restype = C.c_int
     L.mvgd_set_wait_limit.argtypes = [C.c_int64]
     L.mvgd_set_wait_limit.restype = C.c_int
     L.mvgd_test_withhold_arrival.argtypes = [C.c_int32]

@@ -116,9 +116,10 @@ def ell_alloc(n: int, k: int, prec: int, device) -> tuple:
 def assemble(pts: torch.Tensor, nbr: torch.Tensor, *, prec: int = FP64, order: torch.Tensor | None = None,
              delta_kind: int = DELTA_MEAN_NN, delta_m: int = 6, delta_scale: float = 1.0,
              want_h: bool = True, want_status: bool = True, stream=None, out: Operator | None = None,
-             variant: int = LB.ROW_MVGD) -> Operator:
+             variant: int = LB.ROW_MVGD, arith: int = 0) -> Operator:
     """MVGD rows (Sec. 2, Sec. 3.1) for every point into a sliced ELL operator; variant
-    ROW_LS forms the plain least-squares comparator rows instead."""
+    ROW_LS forms the plain least-squares comparator rows instead.  FP32_REFINE rows are
+    formed on the FP32 pipe (arith 0) or in FP64 arithmetic (arith 1)."""
     _require_cuda(pts, torch.float64, "pts")
     _require_cuda(nbr, torch.int32, "nbr")
     n, k = nbr.shape
@@ -134,9 +135,10 @@ def assemble(pts: torch.Tensor, nbr: torch.Tensor, *, prec: int = FP64, order: t
     else:
         op = out
         op.order = order
-    ws = _workspace(L.mvgd_assemble_workspace_bytes(n), pts.device) if order is not None else None
+    need_ws = order is not None or (prec == FP32_REFINE and arith == 0)
+    ws = _workspace(L.mvgd_assemble_workspace_bytes(n), pts.device) if need_ws else None
     rule = LB.DeltaRule(delta_kind, delta_m if delta_kind == DELTA_MEAN_NN else 0, float(delta_scale),
-                        int(variant))
+                        int(variant), int(arith))
     c = op.cstruct()
     LB.check("mvgd_assemble", L.mvgd_assemble(_vp(pts), n, k, _vp(nbr), rule, C.byref(c), _vp(op.h),
                                                _vp(op.status), _vp(op.bad_rows), _vp(ws),
@@ -307,7 +309,7 @@ class SolveResult:
 
 
 def solve(op: Operator, f: torch.Tensor, *, u0: torch.Tensor | None = None, sigma: float = 1.0,
-          rtol: float = 1e-8, maxit: int = 200000, inner_rtol: float = 1e-5, inner_maxit: int = 20000,
+          rtol: float = 1e-8, maxit: int = 200000, inner_rtol: float = 1e-3, inner_maxit: int = 20000,
           max_outer: int = 60, precond: int = 0, cancel: torch.Tensor | None = None, stream=None,
           workspace: torch.Tensor | None = None, sync: bool = True, amg: "Hierarchy | None" = None) -> SolveResult:
     """Solve (sigma I - L) u = f; f, u FP64 [n] or [n][nrhs] in point order.
@@ -436,36 +438,6 @@ def amg_setup(op: Operator, sigma: float = 1.0, stream=None) -> Hierarchy:
     c = op.cstruct()
     LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), float(sigma), _vp(ws), ws.numel(), _stream(stream)))
     return Hierarchy(op.n, op.k, float(sigma), ws, op)
-
-
-def rows_to_sell(a: np.ndarray, w: int) -> np.ndarray:
-    """[n][w] rows -> sliced-ELL storage (slice height 32, slot-major inside a slice), zero padded."""
-    n = a.shape[0]
-    npad = n_padded(n)
-    full = np.zeros((npad, w), dtype=a.dtype)
-    full[:n] = a
-    return np.ascontiguousarray(full.reshape(npad // SLICE, SLICE, w).transpose(0, 2, 1)).ravel()
-
-
-def operator_from_rows(nbr: np.ndarray, val: np.ndarray, prec: int = FP64, device="cuda:0") -> Operator:
-    """An operator from host rows in their own order (no reordering): nbr [n][k]
-    int32, val [n][k+1] FP64 with slot 0 the row itself; FP32_REFINE splits each
-    weight into FP32 hi + lo."""
-    n, k = nbr.shape
-    col, v, lo = ell_alloc(n, k, prec, device)
-    c = rows_to_sell(np.ascontiguousarray(nbr, dtype=np.int32), k)
-    col[: c.size].copy_(torch.from_numpy(c))
-    if prec == FP64:
-        vv = rows_to_sell(np.asarray(val, dtype=np.float64), k + 1)
-        v[: vv.size].copy_(torch.from_numpy(vv))
-    else:
-        hi = np.asarray(val, dtype=np.float64).astype(np.float32)
-        rest = (np.asarray(val, dtype=np.float64) - hi.astype(np.float64)).astype(np.float32)
-        h = rows_to_sell(hi, k + 1)
-        r = rows_to_sell(rest, k + 1)
-        v[: h.size].copy_(torch.from_numpy(h))
-        lo[: r.size].copy_(torch.from_numpy(r))
-    return Operator(n, k, prec, col, v, lo, None)
 
 
 STEP_NAMES = {0: "PRE_A", 1: "A", 2: "PRE_B", 3: "B", 4: "C"}

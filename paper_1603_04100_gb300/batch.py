@@ -45,7 +45,7 @@ class BatchPipeline:
     """Preallocated buffers for a fixed list of (n, k, nrhs) clouds."""
 
     def __init__(self, sizes, *, prec: int = api.FP32_REFINE, device="cuda:0", n_streams: int = 8,
-                 rtol: float = 1e-8, inner_rtol: float = 1e-5, maxit: int = 200000, inner_maxit: int = 20000,
+                 rtol: float = 1e-8, inner_rtol: float = 1e-3, maxit: int = 200000, inner_maxit: int = 20000,
                  max_outer: int = 60, precond: int = 1, delta_m: int = 6, cell_scale: float = 0.0):
         self.device = torch.device(device)
         self.prec = prec

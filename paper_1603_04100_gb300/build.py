@@ -17,7 +17,8 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 OUT_DIR = PKG / "_build"
 LIB = OUT_DIR / "libmvgd.so"
-SOURCES = ("knn.cu", "assemble.cu", "spmv.cu", "solve.cu", "amg.cu", "block.cu", "gs.cu", "neumann.cu", "capi.cu")
+SOURCES = ("knn.cu", "assemble.cu", "spmv.cu", "solve.cu", "amg.cu", "block.cu", "gs.cu", "neumann.cu", "capi.cu",
+           "ritz.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "--expt-relaxed-constexpr"]

@@ -738,23 +738,47 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
         double acc[kChan * QT];
 #pragma unroll
         for (int e = 0; e < kChan * QT; e++) acc[e] = 0.0;
+        // Each thread sums its tiles in increasing order; the loads of kFinUnroll
+        // consecutive strides are issued before any is added, so the sum costs
+        // nchunk / (kThreads * kFinUnroll) dependent L2 round trips, not one per stride.
+        constexpr int kFinUnroll = 4;
         if (P.Q == 1 && (P.nchunk & 1) == 0) {
-            // one right-hand side: two consecutive tiles' partials per (16-byte) load,
-            // half the dependent L2 round trips of the general loop below
-            for (int l = 2 * tid; l < P.nchunk; l += 2 * kThreads)
+            // one right-hand side: two consecutive tiles' partials per (16-byte) load
+            for (int l0 = 2 * tid; l0 < P.nchunk; l0 += 2 * kThreads * kFinUnroll)
 #pragma unroll
                 for (int ch = 0; ch < kChan; ch++) {
-                    const double2 v =
-                        __ldcg(reinterpret_cast<const double2*>(&P.part[((int64_t)slot * kChan + ch) * P.nchunk + l]));
-                    acc[ch * QT] += v.x;
-                    acc[ch * QT] += v.y;
+                    const double* base = &P.part[((int64_t)slot * kChan + ch) * P.nchunk];
+                    double2 v[kFinUnroll];
+#pragma unroll
+                    for (int u = 0; u < kFinUnroll; u++) {
+                        const int l = l0 + u * 2 * kThreads;
+                        v[u] = l < P.nchunk ? __ldcg(reinterpret_cast<const double2*>(base + l)) : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kFinUnroll; u++) {
+                        if (l0 + u * 2 * kThreads >= P.nchunk) break;
+                        acc[ch * QT] += v[u].x;
+                        acc[ch * QT] += v[u].y;
+                    }
                 }
         } else {
-            for (int l = tid; l < P.nchunk; l += kThreads)
+            for (int l0 = tid; l0 < P.nchunk; l0 += kThreads * kFinUnroll)
 #pragma unroll
                 for (int e = 0; e < kChan * QT; e++) {
                     const int ch = e / QT, q = e % QT;
-                    if (q < P.Q) acc[e] += __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q]);
+                    if (q >= P.Q) continue;
+                    double v[kFinUnroll];
+#pragma unroll
+                    for (int u = 0; u < kFinUnroll; u++) {
+                        const int l = l0 + u * kThreads;
+                        v[u] = l < P.nchunk ? __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q])
+                                            : 0.0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kFinUnroll; u++) {
+                        if (l0 + u * kThreads >= P.nchunk) break;
+                        acc[e] += v[u];
+                    }
                 }
         }
 #pragma unroll

@@ -8,9 +8,10 @@ Shift-invert subspace iteration on A = sigma I - L, whose smallest eigenvalues
                        X = Y R^-1 (mvgd_block_combine);
   H = X^T (L X)        mvgd_spmv with sigma = 0, alpha = -1 per block, then a Gram;
 and the Ritz values of the p x p matrix H estimate the eigenvalues of L
-(lambda = -theta).  Every O(n) step runs in the library's kernels; only the
-p x p Cholesky factor and the Ritz values of H (p <= 128) are computed on the
-host, as in reverse-communication eigensolvers.  The operator is not
+(lambda = -theta).  Every O(n) step runs in the library's kernels; the p x p
+Cholesky inverse and the Ritz values of H (p <= 128) run in the library's host
+code (mvgd_block_chol_inverse, mvgd_ritz_values), as in reverse-communication
+eigensolvers.  The operator is not
 symmetric, so H is not either; its eigenvalues near a multiplet of the
 sphere come out real up to rounding, and their real parts are reported.
 """
@@ -75,10 +76,10 @@ class _Kit:
         """X = Y R^-1 with R^T R = Y^T Y, twice (the second pass restores orthogonality)."""
         src = Y
         for _ in range(2):
-            G = self.gram(src, src)
-            G = 0.5 * (G + G.T)
-            R = np.linalg.cholesky(G).T
-            Rinv = np.linalg.solve(R, np.eye(self.p))
+            G = np.ascontiguousarray(self.gram(src, src))
+            Rinv = np.empty((self.p, self.p))
+            LB.check("mvgd_block_chol_inverse", self.L.mvgd_block_chol_inverse(
+                G.ctypes.data_as(C.c_void_p), self.p, Rinv.ctypes.data_as(C.c_void_p)))
             dst = X if src is Y else Y
             self.combine(src, Rinv, dst)
             src = dst
@@ -148,9 +149,11 @@ def _iterate(op, nev, p, st, sigma, tol, maxit, rtol_solve, seed, mask) -> EigRe
             c = op.cstruct()
             LB.check("mvgd_spmv", L.mvgd_spmv(C.byref(c), mode, W, 0.0, -1.0, api._vp(X[b, :n]), 0.0,
                                                 api._vp(Z[b, :n]), api._stream(st)))
-        Hm = kit.gram(X, Z)
-        theta = np.linalg.eigvals(Hm)
-        lam = np.sort(-theta.real)[:nev]
+        Hm = np.ascontiguousarray(kit.gram(X, Z))
+        re, im = np.empty(p), np.empty(p)
+        LB.check("mvgd_ritz_values", L.mvgd_ritz_values(Hm.ctypes.data_as(C.c_void_p), p,
+                                                          re.ctypes.data_as(C.c_void_p), im.ctypes.data_as(C.c_void_p)))
+        lam = np.sort(-re)[:nev]
         if prev is not None:
             change = float(np.max(np.abs(lam - prev) / np.maximum(np.abs(lam), 1.0)))
             if change <= tol:

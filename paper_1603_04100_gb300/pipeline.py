@@ -22,9 +22,9 @@ KERNELS_SOLVE = 9         # init: 2 gathers + state; iterate: table, count, solv
 
 class Pipeline:
     def __init__(self, n: int, k: int, nrhs: int = 1, *, prec: int = api.FP32_REFINE, device="cuda:0",
-                 reorder: bool = True, delta_m: int = 6, rtol: float = 1e-8, inner_rtol: float = 1e-5,
+                 reorder: bool = True, delta_m: int = 6, rtol: float = 1e-8, inner_rtol: float = 1e-3,
                  maxit: int = 200000, inner_maxit: int = 20000, max_outer: int = 60, precond: int = 1,
-                 stream: torch.cuda.Stream | None = None):
+                 stream: torch.cuda.Stream | None = None, arith: int = 0):
         self.n, self.k, self.nrhs, self.prec = n, k, nrhs, prec
         self.device = torch.device(device)
         self.reorder, self.delta_m = reorder, delta_m
@@ -50,7 +50,7 @@ class Pipeline:
         self.info = torch.zeros(nrhs * C.sizeof(LB.SolveInfo), dtype=torch.uint8, device=dev)
         self.opts = LB.SolveOpts(rtol, maxit, inner_maxit, inner_rtol, max_outer, precond,
                                  api._vp(self.ws_amg))
-        self.rule = LB.DeltaRule(api.DELTA_MEAN_NN, delta_m, 1.0)
+        self.rule = LB.DeltaRule(api.DELTA_MEAN_NN, delta_m, 1.0, 0, arith)
         # host-side staging for run_host
         self.pts_dev = torch.empty((n, 3), dtype=torch.float64, device=dev)
         self.f_dev = torch.empty((n, nrhs), dtype=torch.float64, device=dev)

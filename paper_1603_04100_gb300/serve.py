@@ -93,7 +93,7 @@ def amg_setup_kernels(n: int) -> int:
 
 class Server:
     def __init__(self, device="cuda:0", *, hbm_budget: float = 120e9, prec: int = api.FP32_REFINE,
-                 epoch_iters: int = 32, rtol: float = 1e-8, inner_rtol: float = 1e-5, precond: int = 1,
+                 epoch_iters: int = 32, rtol: float = 1e-8, inner_rtol: float = 1e-3, precond: int = 1,
                  maxit: int = 200000, max_active: int = 1024, max_points: int = 1 << 21, max_k: int = 31,
                  pool_streams: int = 4):
         self.device = torch.device(device)

@@ -12,7 +12,7 @@ import pytest
 import oracle
 from oracle import amg as OA
 from paper_1603_04100_gb300 import inputs as I
-from tests.gpu_util import cuda_or_skip
+from tests.gpu_util import cuda_or_skip, operator_from_rows
 from tests.oracle_util import backward_ok, reference_solution, rel_l2
 
 torch = pytest.importorskip("torch")
@@ -35,7 +35,7 @@ def test_hierarchy_matches_oracle(n, k, prec_name):
     from paper_1603_04100_gb300 import api
     prec = getattr(api, prec_name)
     _, nbr, val = _oracle_operator(n, k, 31, "torus" if k == 24 else "sphere")
-    op = api.operator_from_rows(nbr, val, prec, dev)
+    op = operator_from_rows(nbr, val, prec, dev)
     H = api.amg_setup(op, 1.0)
     torch.cuda.synchronize()
     levels = OA.hierarchy(val, nbr, 1.0)
@@ -74,7 +74,7 @@ def test_coarsest_inverse(n):
     dev = cuda_or_skip()
     from paper_1603_04100_gb300 import api
     _, nbr, val = _oracle_operator(n, 20, 32)
-    H = api.amg_setup(api.operator_from_rows(nbr, val, api.FP64, dev), 1.0)
+    H = api.amg_setup(operator_from_rows(nbr, val, api.FP64, dev), 1.0)
     Ac = OA.hierarchy(val, nbr, 1.0)[-1].dense()
     nc = Ac.shape[0]
     want = np.linalg.inv(Ac)
@@ -95,7 +95,7 @@ def test_vcycle_matches_oracle(n, nrhs):
     dev = cuda_or_skip()
     from paper_1603_04100_gb300 import api
     _, nbr, val = _oracle_operator(n, 20, 33)
-    H = api.amg_setup(api.operator_from_rows(nbr, val, api.FP64, dev), 1.0)
+    H = api.amg_setup(operator_from_rows(nbr, val, api.FP64, dev), 1.0)
     levels = OA.hierarchy(val, nbr, 1.0)
     b = np.random.default_rng(5).standard_normal((n, nrhs))
     x = H.apply(torch.from_numpy(b).to(dev)).cpu().numpy()
@@ -120,7 +120,7 @@ def test_multigrid_preconditioned_solve(prec_name):
     prec = getattr(api, prec_name)
     n = 60000
     _, nbr, val, f = _solve_case(n, 20, 34)
-    op = api.operator_from_rows(nbr, val, prec, dev)
+    op = operator_from_rows(nbr, val, prec, dev)
     ft = torch.from_numpy(f).to(dev)
     # several times fewer Krylov iterations than the row-scaled solve
     plain = api.solve(op, ft, rtol=1e-9, precond=1)
@@ -145,7 +145,7 @@ def test_multigrid_solve_of_a_single_level_system_is_direct():
     dev = cuda_or_skip()
     from paper_1603_04100_gb300 import api
     _, nbr, val, f = _solve_case(400, 16, 35)
-    op = api.operator_from_rows(nbr, val, api.FP64, dev)
+    op = operator_from_rows(nbr, val, api.FP64, dev)
     res = api.solve(op, torch.from_numpy(f).to(dev), rtol=1e-10, precond=2)
     assert res.status == [0] and res.iters[0] <= 3, (res.status, res.iters)
 

@@ -107,3 +107,40 @@ def test_dirichlet_hemisphere_eigenvalues_match_oracle():
     assert np.all(np.abs(res.values - want) <= 1e-6 * want), np.abs(res.values - want).max()
     # l (l + 1) with multiplicity l
     assert np.abs(res.values - np.array([2.0, 6, 6, 12, 12, 12, 20, 20, 20, 20])).max() <= 0.1
+
+
+def _hemisphere_table(row: str) -> dict:
+    """Sec. 4.3's hemisphere tables (tests/golden/hemisphere_eigen_errors_sec4_3.txt):
+    E^inf (x 1e-2) by sample size for the row named."""
+    from pathlib import Path
+    rows = {}
+    for line in (Path(__file__).parent / "golden" / "hemisphere_eigen_errors_sec4_3.txt").read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            name, *vals = line.split()
+            rows[name] = [float(v) for v in vals]
+    return dict(zip([int(v) for v in rows["samples"]], rows[row]))
+
+
+def test_dirichlet_hemisphere_lambda182_on_the_device():
+    # the table row lambda = 182 (l = 13, multiplicity 13) needs the 91 lowest
+    # Dirichlet eigenvalues: a basis of 104 vectors
+    dev = cuda_or_skip()
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300.eigs import lowest_eigenpairs
+    n = 4000
+    p, b = I.hemisphere(n, 3)
+    pt, bt = torch.from_numpy(p).to(dev), torch.from_numpy(b).to(dev)
+    nbr_t, ord_t = api.knn(pt, 20, want_order=True)
+    op = api.assemble(pt, nbr_t, prec=api.FP64, order=ord_t)
+    api.dirichlet_rows(op, bt)
+    res = lowest_eigenpairs(op, 91, boundary=bt, maxit=600)
+    assert res.change <= 1e-8, (res.iterations, res.change)
+    nbr = nbr_t.cpu().numpy()
+    val, _, _, _ = oracle.assemble(p, nbr)
+    want = oracle.lb_eigenvalues(oracle.dirichlet_rows(val, b), nbr, 91, boundary=b)
+    assert np.all(np.abs(res.values - want) <= 1e-6 * want), np.abs(res.values - want).max()
+    mult = res.values[78:91]                       # l = 13: eigenvalues 78 .. 90
+    einf = np.abs(mult - 182.0).max() / 182.0
+    printed = _hemisphere_table("dirichlet_Einf_182")[n] * 1e-2
+    # the paper's samples are not ours (its hemisphere sampling is not stated): same order
+    assert 0.3 * printed <= einf <= 6.0 * printed, (einf, printed)

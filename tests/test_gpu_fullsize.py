@@ -24,7 +24,7 @@ import pytest
 import oracle
 from oracle import amg as OA
 from paper_1603_04100_gb300 import inputs as I
-from tests.gpu_util import cuda_or_skip, row_relerr
+from tests.gpu_util import cuda_or_skip, operator_from_rows, row_relerr
 from tests.oracle_util import reference_solution, rel_l2
 
 torch = pytest.importorskip("torch")
@@ -148,7 +148,7 @@ def test_vcycle_full_size_matches_oracle(name, lanes):
             g *= 2
         want_g.append(g)
     assert tuple(want_g) == lanes, want_g
-    op = api.operator_from_rows(nbr_m, val_m, api.FP64, dev)
+    op = operator_from_rows(nbr_m, val_m, api.FP64, dev)
     H = api.amg_setup(op, 1.0)
     torch.cuda.synchronize()
     assert H.info(0).status == 0

@@ -184,3 +184,24 @@ def test_neumann_hemisphere_eigenvalues_end_to_end():
     assert np.all(np.abs(res.values - want) <= 1e-6 * np.maximum(want, 1.0)), np.abs(res.values - want).max()
     exact = np.array([0.0, 2, 2, 6, 6, 6, 12, 12, 12, 12, 20, 20, 20, 20, 20])
     assert np.abs(res.values - exact).max() <= 0.1
+
+
+def test_neumann_hemisphere_lambda182_on_the_device():
+    # the table row lambda = 182 (l = 13, multiplicity 14) needs the 105 lowest
+    # Neumann eigenvalues: a basis of 120 vectors
+    dev = cuda_or_skip()
+    from paper_1603_04100_gb300 import api
+    from paper_1603_04100_gb300.eigs import lowest_eigenpairs
+    from tests.test_gpu_eigs import _hemisphere_table
+    n = 4000
+    p, b = I.hemisphere(n, 3)
+    _, _, _, _, _, _, val, col = _oracle(p, b, 20)
+    op, _ = api.neumann_operator(torch.from_numpy(p).to(dev), torch.from_numpy(b).to(dev), 20, prec=api.FP64)
+    res = lowest_eigenpairs(op, 105, maxit=600)
+    assert res.change <= 1e-8, (res.iterations, res.change)
+    want = oracle.lb_eigenvalues(val, col, 105)
+    assert np.all(np.abs(res.values - want) <= 1e-6 * np.maximum(want, 1.0)), np.abs(res.values - want).max()
+    mult = res.values[91:105]                      # l = 13: eigenvalues 91 .. 104
+    einf = np.abs(mult - 182.0).max() / 182.0
+    printed = _hemisphere_table("neumann_Einf_182")[n] * 1e-2
+    assert 0.3 * printed <= einf <= 6.0 * printed, (einf, printed)
