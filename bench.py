@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--paths", default="fp32_refine+amg,fp64+amg,fp32_refine,fp64",
                     help="comma list of <precision>[+amg] paths to time (the fastest is the headline)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline sample")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched / served / open-surface / eigenvalue lines after the headline")
     ap.add_argument("--profile-case", type=int, nargs=4, metavar=("N", "PREC", "ITERS", "PRECOND"),
@@ -719,12 +720,26 @@ def main():
     names = [p.strip() for p in args.paths.split(",") if p.strip()]
     if args.no_plain:
         names = [p for p in names if p.startswith("fp32_refine")]
+    # launch shapes (kNN cell edge, assembly warps a block, solver blocks a SM and
+    # staged slices) chosen by timing on this cloud, before any timed step; they
+    # change no result (tests/test_gpu_tune.py)
+    from paper_1603_04100_gb300 import tune
+    tuning, tuning_source = tune.Tuning(), "library defaults"
+    if not args.no_tune:
+        cached = tune.shape_key(n, k, api.FP32_REFINE, 2, dev) in tune.load_cache()
+        tp = Pipeline(n, k, 1, prec=api.FP32_REFINE, device=dev, precond=2, rtol=RTOL, stream=stream)
+        with torch.cuda.stream(stream):
+            tuning = tune.tune_pipeline(tp, pts, f)
+        tuning_source = "cache" if cached else "searched on this cloud"
+        del tp
+    tuning.apply()
     results = {}
     with ClockSampler(local) as clk:
         for name in names:
             prec = api.FP32_REFINE if name.startswith("fp32_refine") else api.FP64
             precond = 2 if name.endswith("+amg") else 1
             pipe = Pipeline(n, k, 1, prec=prec, device=dev, precond=precond, rtol=RTOL, stream=stream)
+            pipe.knn_cell = tuning.knn_cell
             rec, _ = timed_runs(pipe, args.steps, args.warmup)
             info = pipe.decode()[0]
             u = pipe.u[:, 0].double().cpu().numpy()
@@ -796,6 +811,7 @@ def main():
         "err_exact_inf": err_exact,
         "gpu_launches": R["pipe"].kernels_per_run * args.steps + args.steps,  # + one flush per step
         "roofline": roofline, "clocks": clocks,
+        "tuning": {**tuning.__dict__, "source": tuning_source},
         "paths": {nm: summary(nm) for nm in results},
     }
     if "fp64" in results:

@@ -63,9 +63,10 @@ int32_t mvgd_version(void);
  * (the cell order of the search grid); pass it to mvgd_assemble so that the
  * solver works on rows whose neighbours are close in memory.
  *
- * cell_size > 0 fixes the edge of the search grid's cells; <= 0 picks one
- * from an estimate of the k-th neighbour distance.  Results never depend on
- * it, only the speed does.
+ * cell_size > 0 fixes the edge of the search grid's cells; 0 picks one from
+ * an estimate of the k-th neighbour distance, and a negative value picks
+ * -cell_size times that estimate (what a tuner varies).  Results never depend
+ * on it, only the speed does.
  * ------------------------------------------------------------------------ */
 size_t mvgd_knn_workspace_bytes(int64_t n, int32_t k);
 mvgd_status mvgd_knn(const double *pts, int64_t n, int32_t k, int32_t *nbr, int32_t *order,
@@ -565,6 +566,21 @@ int32_t mvgd_trace_read(uint64_t *out, int32_t max);
  * ------------------------------------------------------------------------ */
 mvgd_status mvgd_set_wait_limit(int64_t polls);
 mvgd_status mvgd_test_withhold_arrival(int32_t on);
+
+/* ------------------------------------------------------------------------
+ * Launch shapes (for a tuner; the paper has no counterpart).  Process-wide,
+ * for launches made from now on; they change the speed of a call, never its
+ * results (the solver's reductions run over fixed chunks whatever the grid,
+ * and every assembled row is one lane's work whatever the block).
+ *   solver_blocks_per_sm: resident blocks per SM of the persistent solver
+ *     (0: as many as fit, the default; otherwise at most that many);
+ *   stage_buffers: operator slices a solver warp keeps in flight, 1 (default)
+ *     or 2 (used only when the shared memory allows it; 0 = 1);
+ *   assemble_warps: warps per block of the FP32 assembly path, 1 (default),
+ *     2, 4 or 8 (fewer when the shared memory would not fit; 0 = 1); the FP64
+ *     arithmetic always takes one.
+ * MVGD_EINVAL for a value out of range.  Host-side only. */
+mvgd_status mvgd_set_launch_tuning(int32_t solver_blocks_per_sm, int32_t stage_buffers, int32_t assemble_warps);
 
 #ifdef __cplusplus
 }

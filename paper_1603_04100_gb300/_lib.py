@@ -31,7 +31,7 @@ EXPORTS = (
     "mvgd_block_combine", "mvgd_block_zero_rows", "mvgd_gs_power_workspace_bytes", "mvgd_gs_power",
     "mvgd_neumann_ghosts_workspace_bytes", "mvgd_neumann_ghosts", "mvgd_neumann_fold_workspace_bytes",
     "mvgd_neumann_fold", "mvgd_neumann_rhs", "mvgd_set_wait_limit", "mvgd_test_withhold_arrival",
-    "mvgd_block_chol_inverse", "mvgd_ritz_values",
+    "mvgd_block_chol_inverse", "mvgd_ritz_values", "mvgd_set_launch_tuning",
 )
 PRECOND_NONE, PRECOND_ROWSCALE, PRECOND_AMG = 0, 1, 2
 AMG_AGG, AMG_COARSEST, AMG_MAX_WIDTH = 8, 512, 64  # MVGD_AMG_* in include/mvgd.h
@@ -179,6 +179,8 @@ def load(path: str | os.PathLike | None = None) -> C.CDLL:
     L.mvgd_block_chol_inverse.restype = C.c_int
     L.mvgd_ritz_values.argtypes = [_P, C.c_int32, _P, _P]
     L.mvgd_ritz_values.restype = C.c_int
+    L.mvgd_set_launch_tuning.argtypes = [C.c_int32, C.c_int32, C.c_int32]
+    L.mvgd_set_launch_tuning.restype = C.c_int
     L.mvgd_set_wait_limit.argtypes = [C.c_int64]
     L.mvgd_set_wait_limit.restype = C.c_int
     L.mvgd_test_withhold_arrival.argtypes = [C.c_int32]

@@ -73,6 +73,7 @@ struct AsmArgs {
     uint8_t* status;
     int32_t* bad_rows;
     int arith;              // 1: FP64 arithmetic for the FP32_REFINE format too
+    int kcap;               // the K a warp's shared memory is sized for (>= k)
     int2* fix;              // FP32 path: (item, row) handed to the FP64 path
     int32_t* nfix;
 };
@@ -83,8 +84,9 @@ __device__ __noinline__ void assemble_lane(const AsmArgs& A, int64_t row) {
     extern __shared__ double sm[];
     const int lane = threadIdx.x & (kWarp - 1);
     const int k = A.k, m = k + 1;
+    double* smw = sm + (size_t)(threadIdx.x / kWarp) * (size_t)(A.kcap + 1) * kCols * kWarp;  // this warp's part
     // element (r, c) of this lane's design matrix
-#define VM(r, c) sm[((r) * kCols + (c)) * kWarp + lane]
+#define VM(r, c) smw[((r) * kCols + (c)) * kWarp + lane]
 
     const int64_t i = A.order ? (int64_t)A.order[row] : row;
     const double px = A.pts[3 * i], py = A.pts[3 * i + 1], pz = A.pts[3 * i + 2];
@@ -367,8 +369,9 @@ __device__ __noinline__ bool assemble_lane_mixed(const AsmArgs& A, int64_t row) 
     extern __shared__ float smf[];
     const int lane = threadIdx.x & (kWarp - 1);
     const int k = A.k, m = k + 1;
+    float* smw = smf + (size_t)(threadIdx.x / kWarp) * (size_t)A.kcap * kMixCols * kWarp;  // this warp's part
     // element (s, c) of this lane's neighbour table
-#define MF(s, c) smf[((s) * kMixCols + (c)) * kWarp + lane]
+#define MF(s, c) smw[((s) * kMixCols + (c)) * kWarp + lane]
     const int64_t i = A.order ? (int64_t)A.order[row] : row;
     const int32_t* nb = A.nbr + i * k;
     const double px = A.pts[3 * i], py = A.pts[3 * i + 1], pz = A.pts[3 * i + 2];
@@ -577,9 +580,12 @@ __device__ __forceinline__ void assemble_row(const AsmArgs& A, int64_t row, int 
     assemble_lane(A, row);
 }
 
+// A warp per 32-row slice, blockDim.x / 32 warps a block (the launch's tuning).
 template <int MODE>
-__global__ void __launch_bounds__(32) k_assemble(AsmArgs A) {
-    assemble_row<MODE>(A, blockIdx.x * (int64_t)kSlice + threadIdx.x, 0);
+__global__ void __launch_bounds__(256) k_assemble(AsmArgs A) {
+    const int64_t slice = (int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp;
+    if (slice * kSlice >= n_padded(A.n)) return;
+    assemble_row<MODE>(A, slice * kSlice + (threadIdx.x & (kWarp - 1)), 0);
 }
 
 // The rows the FP32 path handed over, by the FP64 path: a lane per row.
@@ -735,6 +741,7 @@ MVGD_API mvgd_status mvgd_assemble(const double* pts, int64_t n, int32_t k, cons
     A.col = L->col; A.val = L->val; A.val_lo = L->val_lo;
     A.h_out = h; A.status = row_status; A.bad_rows = bad_rows;
     A.arith = rule.arith;
+    A.kcap = k;
     A.fix = mixed ? W.fix : nullptr;
     A.nfix = mixed ? W.nfix : nullptr;
     if (bad_rows) MVGD_CUDA_TRY(cudaMemsetAsync(bad_rows, 0, sizeof(int32_t), s));
@@ -742,18 +749,25 @@ MVGD_API mvgd_status mvgd_assemble(const double* pts, int64_t n, int32_t k, cons
     if (gb > 4096) gb = 4096;
     if (L->order) k_invert_order<<<gb, 256, 0, s>>>(L->order, n, W.inv);
     const int64_t nslices = n_padded(n) / kSlice;
+    // warps a block: the launch's tuning for the FP32 path (15 KB of shared memory a
+    // warp); the FP64 arithmetic keeps one (38 KB a warp: more would only cost
+    // resident warps)
+    int wpb = mixed ? tuned_assemble_warps() : 1;
+    const size_t per_warp = mixed ? smem_mixed(k) : smem_fp64(k);
+    while (wpb > 1 && per_warp * wpb > (size_t)(200 << 10)) wpb >>= 1;
+    const unsigned blocks = (unsigned)((nslices + wpb - 1) / wpb);
     if (mixed) {
         MVGD_CUDA_TRY(cudaMemsetAsync(W.nfix, 0, sizeof(int32_t), s));
-        const size_t sm = smem_mixed(k);
+        const size_t sm = per_warp * wpb;
         MVGD_CUDA_TRY(cudaFuncSetAttribute(k_assemble<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_assemble<1><<<(unsigned)nslices, kWarp, sm, s>>>(A);
+        k_assemble<1><<<blocks, kWarp * wpb, sm, s>>>(A);
         const size_t sf = smem_fp64(k);
         MVGD_CUDA_TRY(cudaFuncSetAttribute(k_assemble_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
         k_assemble_fix<<<kFixBlocks, kWarp, sf, s>>>(A);
     } else {
-        const size_t sf = smem_fp64(k);
+        const size_t sf = per_warp * wpb;
         MVGD_CUDA_TRY(cudaFuncSetAttribute(k_assemble<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf));
-        k_assemble<0><<<(unsigned)nslices, kWarp, sf, s>>>(A);
+        k_assemble<0><<<blocks, kWarp * wpb, sf, s>>>(A);
     }
     return launch_status();
 }
@@ -844,6 +858,7 @@ MVGD_API mvgd_status mvgd_assemble_batch(const mvgd_assemble_item* items, int32_
         a.a.status = it.row_status;
         a.a.bad_rows = bad_rows;
         a.a.arith = mixed ? 0 : 1;  // an FP32_REFINE item below kMinKMixed takes the FP64 path
+        a.a.kcap = kmax;
         a.a.fix = mixed ? fix : nullptr;
         a.a.nfix = mixed ? nfix : nullptr;
         a.slice0 = slices;

@@ -54,6 +54,10 @@ inline mvgd_status launch_status() {
 // one), and the one-shot withhold control (true once after it was armed).
 long long wait_limit_or(long long dflt);
 bool take_withhold();
+// Launch shapes set by mvgd_set_launch_tuning (speed only, never results).
+int tuned_solver_blocks_per_sm();  // 0: as many as fit
+int tuned_stage_buffers();         // 1 or 2
+int tuned_assemble_warps();        // 1, 2, 4 or 8
 
 // ---------------------------------------------------------------------------
 // Warp helpers

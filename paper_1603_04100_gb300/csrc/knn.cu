@@ -203,7 +203,7 @@ __global__ void k_params(const unsigned* __restrict__ bits, int64_t n, int k, do
         double s0 = e / kOccBits;
         double area = (double)occ * s0 * s0 / 1.5;
         double rk = sqrt((double)k * area / (3.141592653589793 * (double)n));
-        s = 1.25 * rk;
+        s = 1.25 * rk * (cell_size < 0 ? -cell_size : 1.0);  // a negative cell_size scales the estimate
     }
     if (!(s > 0) || !isfinite(s)) s = e > 0 ? e : 1.0;
     if (e > 0 && s < e * 1e-6) s = e * 1e-6;   // keep cell coordinates below 2^20

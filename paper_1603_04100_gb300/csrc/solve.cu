@@ -1406,15 +1406,14 @@ __global__ void k_poll(TableArgs A, int32_t* done) {
     }
 }
 
-// Slice buffers per warp.  One: a second buffer (the next tile's slice
-// requested ahead) costs a resident block per SM, and on GB300 at 1M rows,
-// K = 20, three single-buffered blocks ran the FP32 multigrid solve 8 %
+// Slice buffers per warp.  One by default: a second buffer (the next tile's
+// slice requested ahead) costs a resident block per SM, and on GB300 at 1M
+// rows, K = 20, three single-buffered blocks ran the FP32 multigrid solve 8 %
 // faster than two double-buffered ones (every step that is not a product
-// loses the third block's latency hiding).  MVGD_STAGE_BUFFERS=2 selects two.
+// loses the third block's latency hiding).  mvgd_set_launch_tuning selects two.
 template <typename VT>
 int stage_buffers(int kmax) {
-    const char* e = getenv("MVGD_STAGE_BUFFERS");
-    if (e && e[0] == '2' && e[1] == 0 && 2 * stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp) <= (112u << 10))
+    if (tuned_stage_buffers() == 2 && 2 * stage_bytes_per_warp<VT>(kmax) * (kThreads / kWarp) <= (112u << 10))
         return 2;
     return 1;
 }
@@ -1431,6 +1430,8 @@ mvgd_status launch_solve(const ReqTable& tab, Ctl ctl, int budget, int kmax, cud
     MVGD_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     MVGD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kThreads, smem));
     if (per_sm < 1) return MVGD_ECUDA;
+    const int want = tuned_solver_blocks_per_sm();
+    if (want > 0 && want < per_sm) per_sm = want;
     int grid = sms * per_sm;
     if (grid > tab.fine.nchunks) grid = tab.fine.nchunks;
     ReqTable t = tab;

@@ -54,6 +54,9 @@ class Pipeline:
         # host-side staging for run_host
         self.pts_dev = torch.empty((n, 3), dtype=torch.float64, device=dev)
         self.f_dev = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
+        # the kNN grid's cell edge argument (0: the library's estimate; a tuner sets a
+        # negative multiple of it, see tune.py)
+        self.knn_cell = 0.0
 
     @property
     def kernels_per_run(self) -> int:
@@ -74,31 +77,56 @@ class Pipeline:
         """Enqueue kNN + assembly + solve on the stream; returns the device info buffer."""
         return self.run_staged(pts, f, None)
 
-    def run_staged(self, pts: torch.Tensor, f: torch.Tensor, events=None) -> torch.Tensor:
-        """As run(); events[1] / events[2] / events[3] (if given) are recorded after kNN /
-        assembly / the multigrid set-up (right after assembly without one)."""
+    def _stream(self):
+        return self.stream if self.stream is not None else torch.cuda.current_stream()
+
+    def knn_call(self, pts: torch.Tensor) -> None:
         L = LB.load()
-        st = self.stream if self.stream is not None else torch.cuda.current_stream()
-        s = api._stream(st)
         vp = api._vp
-        LB.check("mvgd_knn", L.mvgd_knn(vp(pts), self.n, self.k, vp(self.nbr), vp(self.order), 0.0,
-                                         vp(self.ws_knn), self.ws_knn.numel(), s))
-        if events is not None:
-            events[1].record(st)
+        LB.check("mvgd_knn", L.mvgd_knn(vp(pts), self.n, self.k, vp(self.nbr), vp(self.order), float(self.knn_cell),
+                                         vp(self.ws_knn), self.ws_knn.numel(), api._stream(self._stream())))
+
+    def assemble_call(self, pts: torch.Tensor) -> None:
+        L = LB.load()
+        vp = api._vp
         c = self.op.cstruct()
         LB.check("mvgd_assemble", L.mvgd_assemble(vp(pts), self.n, self.k, vp(self.nbr), self.rule, C.byref(c),
                                                    None, None, vp(self.op.bad_rows), vp(self.ws_asm),
-                                                   self.ws_asm.numel(), s))
-        if events is not None:
-            events[2].record(st)
+                                                   self.ws_asm.numel(), api._stream(self._stream())))
+
+    def amg_call(self) -> None:
+        if self.ws_amg is None:
+            return
+        L = LB.load()
+        c = self.op.cstruct()
+        LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, api._vp(self.ws_amg), self.ws_amg.numel(),
+                                                     api._stream(self._stream())))
+
+    def solve_call(self, f: torch.Tensor) -> None:
+        L = LB.load()
+        vp = api._vp
+        st = self._stream()
         with torch.cuda.stream(st):
             self.u.zero_()
-        if self.ws_amg is not None:
-            LB.check("mvgd_amg_setup", L.mvgd_amg_setup(C.byref(c), 1.0, vp(self.ws_amg), self.ws_amg.numel(), s))
+        c = self.op.cstruct()
+        LB.check("mvgd_solve", L.mvgd_solve(C.byref(c), self.nrhs, 1.0, vp(f), vp(self.u), C.byref(self.opts),
+                                             vp(self.info), None, vp(self.ws_solve), self.ws_solve.numel(),
+                                             api._stream(st)))
+
+    def run_staged(self, pts: torch.Tensor, f: torch.Tensor, events=None) -> torch.Tensor:
+        """As run(); events[1] / events[2] / events[3] (if given) are recorded after kNN /
+        assembly / the multigrid set-up (right after assembly without one)."""
+        st = self._stream()
+        self.knn_call(pts)
+        if events is not None:
+            events[1].record(st)
+        self.assemble_call(pts)
+        if events is not None:
+            events[2].record(st)
+        self.amg_call()
         if events is not None and len(events) > 4:
             events[3].record(st)
-        LB.check("mvgd_solve", L.mvgd_solve(C.byref(c), self.nrhs, 1.0, vp(f), vp(self.u), C.byref(self.opts),
-                                             vp(self.info), None, vp(self.ws_solve), self.ws_solve.numel(), s))
+        self.solve_call(f)
         return self.info
 
     def run_host(self, pts_host: torch.Tensor, f_host: torch.Tensor, u_host: torch.Tensor) -> None:

@@ -89,3 +89,25 @@ def test_mvgd_inside_unit_circle_least_squares_outside():
         est = float(np.exp(np.mean(np.log(nu[200:]))))
         assert abs(est - rho[variant]) <= 1e-3 * rho[variant], (variant, est, rho[variant])
     assert rho[oracle.VARIANT_MVGD] < 1.0 < 5.0 < rho[oracle.VARIANT_LS], rho
+
+
+def test_least_squares_system_is_indefinite_mvgd_is_not():
+    # Sec. 4.1's conditioning contrast, on the system the solver sees, A = I - L:
+    # on the Fibonacci sphere (2,562 points, K = 12) the MVGD rows give eigenvalues
+    # of positive real part near the origin (the smallest is 1, the constants),
+    # the least-squares rows eigenvalues of negative real part too -- an indefinite,
+    # nonnormal system on which restarted GMRES stagnates and BiCGSTAB diverges
+    import scipy.sparse.linalg as spl
+    pts = I.fibonacci_sphere(2562)
+    nbr = oracle.knn_grid(pts, 12)
+    for variant, indefinite in ((oracle.VARIANT_MVGD, False), (oracle.VARIANT_LS, True)):
+        val, st, _, _ = oracle.assemble(pts, nbr, variant=variant)
+        A = oracle.system_matrix(val, nbr, 1.0).tocsc()
+        ev = spl.eigs(A, k=6, sigma=0.0, which="LM", return_eigenvectors=False)
+        assert (ev.real.min() < 0.0) == indefinite, (variant, np.sort_complex(ev))
+        if not indefinite:
+            assert abs(ev.real.min() - 1.0) < 1e-8   # the constant vector: (I - L) 1 = 1
+    # the oracle's GMRES(30) on the least-squares system: the residual stalls far above 1e-8
+    val, _, _, _ = oracle.assemble(pts, nbr, variant=oracle.VARIANT_LS)
+    _, it, rel, status = oracle.gmres(val, nbr, 3.0 * pts[:, 0], rtol=1e-8, maxit=3000, restart=30)
+    assert status != 0 and 1e-6 < rel < 1e-2, (it, rel)
