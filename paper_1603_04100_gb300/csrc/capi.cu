@@ -16,6 +16,7 @@ int tuned_solver_blocks_per_sm() { return g_solver_blocks.load(); }
 int tuned_stage_buffers() { return g_stage_buffers.load(); }
 int tuned_assemble_warps() { return g_assemble_warps.load(); }
 
+
 long long wait_limit_or(long long dflt) {
     const long long v = g_wait_limit.load();
     return v > 0 ? v : dflt;

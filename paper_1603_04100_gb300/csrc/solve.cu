@@ -944,7 +944,10 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             if (staged) {
                 int64_t slice2 = 0;
                 const int cn = next_tile(tab.fine, c, ri, P.n, wid, slice2);
-                const int b = st.acquire(c, slice, cn, slice2, P.col, P.val, (int)sizeof(VT), P.k, ctl.err);
+                // FP32 multigrid flow: the hierarchy's level-0 weights (the operator's hi
+                // values, copied at set-up), the array the V-cycle's level-0 steps read too
+                const void* vsrc = (AMG && MIXED) ? static_cast<const void*>(P.amg->lv[0].val) : P.val;
+                const int b = st.acquire(c, slice, cn, slice2, P.col, vsrc, (int)sizeof(VT), P.k, ctl.err);
                 const int* colS = st.col(b);
                 const VT* valS = static_cast<const VT*>(st.val(b));
                 auto landed = [&]() { return st.wait(b, ctl.err); };
