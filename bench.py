@@ -503,13 +503,16 @@ def batched_measure(dev, reps, specs, steps: int, warmup: int, arms=(("fp32_refi
             bp.run(pts, fs)
         reps.barrier()
         ms = []
+        stages = {"knn": [], "assemble": [], "amg_setup": [], "solve": []}
         for _ in range(max(1, steps)):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            bp.run(pts, fs)
-            e1.record()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            ev[0].record()
+            bp.run(pts, fs, marks=ev[1:4])
+            ev[4].record()
             torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
+            ms.append(ev[0].elapsed_time(ev[4]))
+            for j, key in enumerate(stages):
+                stages[key].append(ev[j].elapsed_time(ev[j + 1]))
         reps.barrier()
         ms_max = reps.max(statistics.mean(ms))
         infos = bp.infos()
@@ -522,7 +525,8 @@ def batched_measure(dev, reps, specs, steps: int, warmup: int, arms=(("fp32_refi
                               "mean_iters": statistics.mean(iters),
                               "converged_clouds": sum(conv), "converged_points": sum(
                                   s[0] for s, c in zip(sizes, conv) if c),
-                              "gpu_launches": bp.kernels_per_run}
+                              "gpu_launches": bp.kernels_per_run,
+                              "stage_ms": {key: statistics.mean(v) for key, v in stages.items()}}
         del bp
         torch.cuda.empty_cache()
     # plain: the same clouds one at a time, FP64 with row scaling

@@ -94,8 +94,10 @@ class BatchPipeline:
     def total_points(self) -> int:
         return sum(s.n for s in self.slots)
 
-    def run(self, pts_list, f_list, cancel: torch.Tensor | None = None):
-        """Enqueue kNN + assembly + solve for every cloud on the current stream."""
+    def run(self, pts_list, f_list, cancel: torch.Tensor | None = None, marks=None):
+        """Enqueue kNN + assembly + solve for every cloud on the current stream.  If given,
+        marks[0] / [1] / [2] (CUDA events) are recorded on it once every cloud's kNN, the
+        batched assembly and every multigrid set-up have been enqueued before them."""
         L = LB.load()
         vp = api._vp
         main = torch.cuda.current_stream(self.device)
@@ -112,12 +114,16 @@ class BatchPipeline:
             ev = torch.cuda.Event()
             ev.record(st)
             main.wait_event(ev)
+        if marks is not None:
+            marks[0].record(main)
         items = (LB.AssembleItem * len(self.slots))()
         for i, (slot, pts) in enumerate(zip(self.slots, pts_list)):
             items[i] = LB.AssembleItem(vp(pts), vp(slot.nbr), slot.op.cstruct(), C.c_void_p(0), C.c_void_p(0))
         s = api._stream(main)
         LB.check("mvgd_assemble_batch", L.mvgd_assemble_batch(items, len(self.slots), self.rule, vp(self.bad_rows),
                                                                vp(self.asm_ws), self.asm_ws.numel(), s))
+        if marks is not None:
+            marks[1].record(main)
         if self.precond == LB.PRECOND_AMG:
             # the hierarchies on the stream pool: each set-up is a chain of small
             # launches (the coarsest inverse is one block), so clouds overlap
@@ -133,6 +139,8 @@ class BatchPipeline:
                 ev = torch.cuda.Event()
                 ev.record(st)
                 main.wait_event(ev)
+        if marks is not None:
+            marks[2].record(main)
         for slot, f, opts in zip(self.slots, f_list, self._opts):
             c = slot.op.cstruct()
             LB.check("mvgd_request_init", L.mvgd_request_init(vp(slot.req_ws), slot.req_ws.numel(), C.byref(c),

@@ -722,75 +722,61 @@ __host__ __device__ constexpr size_t stage_bytes_per_warp(int kmax) {
 
 // This block has finished `cnt` tiles of request P in a reducing phase: publish
 // them (one fence and one atomic per block and request), and if they were the
-// request's last tiles, sum all its tile partials in tile order and advance the
-// per-RHS state.
+// request's last tiles, sum all its tile partials and advance the per-RHS state.
+// The sum's order depends on the tile count alone: thread t takes tiles t,
+// t + 256, ... in batches of kFinBatch whose loads are all issued before any
+// is added, each batch summed as a balanced pairwise tree, the batches in
+// order; then a butterfly over the warp and a pairwise tree over the 8 warps.
+// The dependent chain is log-depth (FP64 additions have a long latency here)
+// and costs one L2 round trip a batch.
 template <bool MIXED, int QT>
 __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int slot, int cnt, const RhsState* S,
                                                     double (&fin)[kThreads / 32][kChan * QT],
                                                     double (&tot)[kChan * QT], int* last, const Ctl& ctl) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    __threadfence();
+    // the block's partial stores precede the barrier; thread 0's fence releases
+    // them (cumulatively) with the arrival, and on the last arrival its second
+    // fence orders every block's partials before the loads below
     __syncthreads();
-    if (tid == 0) *last = (atomicAdd(&P.arrive[slot], (unsigned)cnt) + (unsigned)cnt == (unsigned)P.nchunk);
+    if (tid == 0) {
+        __threadfence();
+        const bool lst = atomicAdd(&P.arrive[slot], (unsigned)cnt) + (unsigned)cnt == (unsigned)P.nchunk;
+        if (lst) __threadfence();
+        *last = lst;
+    }
     __syncthreads();
     if (*last) {
-        __threadfence();
-        double acc[kChan * QT];
-#pragma unroll
-        for (int e = 0; e < kChan * QT; e++) acc[e] = 0.0;
-        // Each thread sums its tiles in increasing order; the loads of kFinUnroll
-        // consecutive strides are issued before any is added, so the sum costs
-        // nchunk / (kThreads * kFinUnroll) dependent L2 round trips, not one per stride.
-        constexpr int kFinUnroll = 4;
-        if (P.Q == 1 && (P.nchunk & 1) == 0) {
-            // one right-hand side: two consecutive tiles' partials per (16-byte) load
-            for (int l0 = 2 * tid; l0 < P.nchunk; l0 += 2 * kThreads * kFinUnroll)
-#pragma unroll
-                for (int ch = 0; ch < kChan; ch++) {
-                    const double* base = &P.part[((int64_t)slot * kChan + ch) * P.nchunk];
-                    double2 v[kFinUnroll];
-#pragma unroll
-                    for (int u = 0; u < kFinUnroll; u++) {
-                        const int l = l0 + u * 2 * kThreads;
-                        v[u] = l < P.nchunk ? __ldcg(reinterpret_cast<const double2*>(base + l)) : make_double2(0.0, 0.0);
-                    }
-#pragma unroll
-                    for (int u = 0; u < kFinUnroll; u++) {
-                        if (l0 + u * 2 * kThreads >= P.nchunk) break;
-                        acc[ch * QT] += v[u].x;
-                        acc[ch * QT] += v[u].y;
-                    }
-                }
-        } else {
-            for (int l0 = tid; l0 < P.nchunk; l0 += kThreads * kFinUnroll)
-#pragma unroll
-                for (int e = 0; e < kChan * QT; e++) {
-                    const int ch = e / QT, q = e % QT;
-                    if (q >= P.Q) continue;
-                    double v[kFinUnroll];
-#pragma unroll
-                    for (int u = 0; u < kFinUnroll; u++) {
-                        const int l = l0 + u * kThreads;
-                        v[u] = l < P.nchunk ? __ldcg(&P.part[(((int64_t)slot * kChan + ch) * P.nchunk + l) * P.Q + q])
-                                            : 0.0;
-                    }
-#pragma unroll
-                    for (int u = 0; u < kFinUnroll; u++) {
-                        if (l0 + u * kThreads >= P.nchunk) break;
-                        acc[e] += v[u];
-                    }
-                }
-        }
+        constexpr int kFinBatch = 16;
+        const int nchunk = P.nchunk, Q = P.Q;
 #pragma unroll
         for (int e = 0; e < kChan * QT; e++) {
-            const double v = warp_sum(acc[e]);
-            if (lane == 0) fin[wid][e] = v;
+            const int ch = e / QT, q = e % QT;
+            double acc = 0.0;
+            if (q < Q) {
+                const double* base = &P.part[((int64_t)slot * kChan + ch) * nchunk * Q + q];
+                for (int l0 = tid; l0 < nchunk; l0 += kThreads * kFinBatch) {
+                    double v[kFinBatch];
+#pragma unroll
+                    for (int u = 0; u < kFinBatch; u++) {
+                        const int l = l0 + u * kThreads;
+                        v[u] = l < nchunk ? __ldcg(base + (int64_t)l * Q) : 0.0;
+                    }
+#pragma unroll
+                    for (int w = 1; w < kFinBatch; w <<= 1)
+#pragma unroll
+                        for (int u = 0; u < kFinBatch; u += 2 * w) v[u] += v[u + w];
+                    acc += v[0];
+                }
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) fin[wid][e] = acc;
         }
         __syncthreads();
+        static_assert(kThreads / 32 == 8, "the warp tree below sums 8 warps");
         if (tid < kChan * QT) {
-            double v = 0.0;
-            for (int w = 0; w < kThreads / 32; w++) v += fin[w][tid];
-            tot[tid] = v;
+            const double* f = &fin[0][tid];
+            constexpr int W = kChan * QT;
+            tot[tid] = ((f[0] + f[W]) + (f[2 * W] + f[3 * W])) + ((f[4 * W] + f[5 * W]) + (f[6 * W] + f[7 * W]));
         }
         __syncthreads();
         if (tid < P.Q) {
@@ -798,8 +784,9 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
             advance<MIXED>(P, ph, T, tot[0 * QT + tid], tot[1 * QT + tid], ctl);
             P.st[tid] = T;
         }
+        // the grid barrier that ends this phase releases the new states and the
+        // reset counter before any block reads them
         if (tid == 0) P.arrive[slot] = 0;
-        __threadfence();
     }
     __syncthreads();
 }
