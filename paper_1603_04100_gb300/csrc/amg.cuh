@@ -57,18 +57,33 @@ struct AmgHeader {
     size_t bytes;       // whole hierarchy
 };
 
-// Lanes that share one row of level l >= 1 in a V-cycle step, a function of the
-// level's size alone (so a request's arithmetic does not depend on what else
-// shares the launch).  A coarse row holds 10-60 entries; one lane per row makes
-// each step a chain of that many dependent L2 round trips on a level too small
-// to fill the GPU, so a level takes the largest G (a power of two, <= 32) that
-// keeps rows x G within one pass of 152 SMs x 3 blocks x 256 threads.  A block
-// of 256 threads takes 256 / G rows: always whole aggregates.
+// Lanes of a row of level l >= 1 in a V-cycle step.  A coarse row holds 10-60
+// entries; one lane per row makes each step a chain of that many dependent L2
+// round trips on a level too small to fill the GPU, so a level of `rows` rows
+// takes amg_group(rows) lanes a row: the largest power of two <= 32 that keeps
+// rows x G within one pass of 152 SMs x 3 blocks x 256 threads.
+//  - The product's arithmetic follows V = amg_group(n_l) of the request's own
+//    level ("virtual lanes", al_row), so a request's result does not depend on
+//    what else shares the launch.
+//  - The lanes that take a row in a launch are G = max(amg_group(launch's rows
+//    at level l), V Q / kAmgMaxPerLane) <= V (Q: the launch's widest request,
+//    whose right-hand sides a lane takes at once): a batch of small requests
+//    is not cut into units of a few rows each, and no lane holds more than
+//    kAmgMaxPerLane partial sums.  Alone with one right-hand side, G = V.
+// A block of 256 threads takes 256 / G rows: always whole aggregates.
+constexpr int kAmgMaxPerLane = 8;
 constexpr int64_t kAmgLanesOnePass = 152 * 3 * 256;
 __host__ __device__ inline int amg_group(int64_t rows) {
     int g = 1;
     while (g < 32 && rows * 2 * g <= kAmgLanesOnePass) g *= 2;
     return g;
+}
+__host__ __device__ inline int amg_lanes(int launch_group, int64_t own_rows, int nrhs) {
+    const int v = amg_group(own_rows);
+    // virtual lanes a lane holds, times the right-hand sides it takes at once, <= kAmgMaxPerLane
+    const int per_lane = kAmgMaxPerLane / nrhs > 1 ? kAmgMaxPerLane / nrhs : 1;
+    const int g = v / per_lane;
+    return launch_group > g ? (launch_group < v ? launch_group : v) : (g > 1 ? g : 1);
 }
 
 // Level sizes for a fine size n: n_0 = n, n_{l+1} = ceil(n_l / kAmgAgg) while

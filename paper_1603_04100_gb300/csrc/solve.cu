@@ -40,7 +40,9 @@ namespace {
 
 constexpr int kCh = 256;   // rows per tile: one per thread, 8 slices of 32
 constexpr int kThreads = 256;
-constexpr int kChan = 2;
+constexpr int kChan = 2;     // reduced channels a step of the row-scaled flows
+constexpr int kChanAmg = 5;  // ... of the multigrid flow (B takes five dot products)
+__host__ __device__ constexpr int chan_count(bool amg) { return amg ? kChanAmg : kChan; }
 constexpr int kRedSlots = 3;
 constexpr int kMaxReq = 1024;
 constexpr long long kStageWaitLimit = 1ll << 24;  // polls of an mbarrier: far beyond any copy's landing time
@@ -206,6 +208,88 @@ __device__ __forceinline__ void c_row_f64(const Prob& P, int64_t r, const RhsSta
         static_cast<double*>(P.r)[e] = rn;
         ad[0][q] += static_cast<const double*>(P.rh)[e] * rn;
         ad[1][q] += rn * rn;
+    }
+}
+
+// Warp totals of E F2 values a lane (E a power of two, at most 32) with a
+// fraction of the shuffles of E separate butterflies.  At each of the first
+// log2 E offsets (16, 8, ...) a lane keeps half of its values -- the upper
+// half if its bit at that offset is set -- and adds the partner's copy of
+// them; the remaining offsets add the one value left.  Every value is summed
+// in exactly the pairs and order of a plain xor butterfly over offsets 16, 8,
+// 4, 2, 1 (f2_add is commutative), so the totals are those of E separate
+// butterflies, bit for bit.  Returns the total of channel `chan` (set here)
+// that this lane ends with; lanes L with L % (32 / E) == 0 hold channels
+// 0 .. E-1 once each.
+template <int E>
+__device__ __forceinline__ F2 warp_sum_f2_multi(F2 (&v)[E], int lane, int& chan) {
+    static_assert(E >= 1 && E <= 32 && (E & (E - 1)) == 0, "a power of two, at most 32 values");
+    chan = 0;
+#pragma unroll
+    for (int t = 0; t < 5; t++) {
+        const int o = 16 >> t;
+        const int h = E >> (t + 1);  // values kept after this offset (0: one value left)
+        if (h >= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < (h >= 1 ? h : 1); j++) {
+                const F2 send = up ? v[j] : v[j + h];
+                const F2 keep = up ? v[j + h] : v[j];
+                F2 recv;
+                recv.hi = __shfl_xor_sync(0xffffffffu, send.hi, o);
+                recv.lo = __shfl_xor_sync(0xffffffffu, send.lo, o);
+                v[j] = f2_add(keep, recv);
+            }
+            if (up) chan += h;
+        } else {
+            F2 w;
+            w.hi = __shfl_xor_sync(0xffffffffu, v[0].hi, o);
+            w.lo = __shfl_xor_sync(0xffffffffu, v[0].lo, o);
+            v[0] = f2_add(v[0], w);
+        }
+    }
+    return v[0];
+}
+
+__host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+
+// A warp's partials of its slice of a tile, channels 0 .. NCH-1 of every
+// right-hand side, into out[ch * QT + q]: the FP32 (F2) products summed over
+// the warp, plus the FP64 ones where there are any (`with64`).
+template <bool MIXED, int QT, int NC, int NCH>
+__device__ __forceinline__ void tile_partials(const F2 (&af)[NC][QT], const double (&ad)[NC][QT], bool with64,
+                                              int lane, double* out) {
+    constexpr int E = pow2_at_least(NCH * QT);
+    double w64[NCH * QT];
+#pragma unroll
+    for (int e = 0; e < NCH * QT; e++) w64[e] = with64 ? warp_sum(ad[e / QT][e % QT]) : 0.0;
+    if constexpr (MIXED && E > 32) {  // more values than lanes: one butterfly each
+#pragma unroll
+        for (int e = 0; e < NCH * QT; e++) {
+            const double x = f2_to_double(warp_sum_f2(af[e / QT][e % QT])) + w64[e];
+            if (lane == 0) out[e] = x;
+        }
+    } else if constexpr (MIXED) {
+        constexpr int E32 = E > 32 ? 32 : E;
+        F2 v[E32];
+#pragma unroll
+        for (int e = 0; e < E32; e++) {
+            v[e].hi = 0.0f;
+            v[e].lo = 0.0f;
+            if (e < NCH * QT) v[e] = af[e / QT][e % QT];
+        }
+        int chan;
+        const F2 tot = warp_sum_f2_multi<E32>(v, lane, chan);
+        if ((lane & (32 / E32 - 1)) == 0 && chan < NCH * QT) {
+            double x = f2_to_double(tot);
+#pragma unroll
+            for (int e = 0; e < NCH * QT; e++)
+                if (e == chan) x += w64[e];
+            out[chan] = x;
+        }
+    } else if (lane == 0) {
+#pragma unroll
+        for (int e = 0; e < NCH * QT; e++) out[e] = w64[e];
     }
 }
 
@@ -382,10 +466,12 @@ __device__ __forceinline__ void spmv_row(const Prob& P, int64_t r, bool valid, i
     }
 }
 
-// RESTART steps A (FP64 true residual) and B (restart the Krylov vectors).
-template <bool MIXED, int QT>
+// RESTART steps: in A the FP64 true residual, in the step that ends the
+// iteration (C of the row-scaled flows, B of the multigrid flow) the restart of
+// the Krylov vectors.
+template <bool MIXED, int QT, int NC>
 __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, const RhsState* S, const bool (&on)[QT],
-                                            double (&ad)[kChan][QT]) {
+                                            double (&ad)[NC][QT]) {
     using VT = typename std::conditional<MIXED, float, double>::type;
     const int Q = P.Q, k = P.k, m = k + 1;
     const int64_t vb = (r / kSlice) * (int64_t)(kSlice * m) + (r % kSlice);
@@ -423,7 +509,7 @@ __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, co
         }
         return;
     }
-    // ph == P_C: restart the Krylov vectors
+    // the iteration's last step: restart the Krylov vectors
     const double invd = P.precond ? (double)static_cast<const VT*>(P.invd)[r] : 1.0;
 #pragma unroll
     for (int q = 0; q < QT; q++) {
@@ -463,6 +549,12 @@ __device__ __forceinline__ void restart_row(const Prob& P, int64_t r, int ph, co
 //   x += alpha ph + omega sh;    r = s - omega t
 // with M^-1 one V-cycle.  p and s are materialised (the cycle reads them at
 // other rows), with their pre-smoothed FP32 copies y_0 = d_0 p for level 0.
+// An iteration has six grid steps, PRE_A, (cycle), A, PRE_B, (cycle), B: the
+// new residual's two dot products follow from those of s and t,
+//   (rh, r) = (rh, s) - omega (rh, t),
+//   (r, r)  = (s, s) - 2 omega (t, s) + omega^2 (t, t),
+// so B takes all five and r = s - omega t is formed by the next PRE_A, row by
+// row, with no step (and no grid barrier) of its own.
 // ------------------------------------------------------------------------------
 template <bool MIXED, int QT>
 __device__ __forceinline__ void amg_pre_row(const Prob& P, int64_t r, int ph, const RhsState* S,
@@ -472,21 +564,27 @@ __device__ __forceinline__ void amg_pre_row(const Prob& P, int64_t r, int ph, co
     const float d0 = P.amg->lv[0].dinv[r];
     VT* pv = static_cast<VT*>(P.p[0]);
     const VT* vv = static_cast<const VT*>(P.v[0]);
-    const VT* rv = static_cast<const VT*>(P.r);
+    VT* rv = static_cast<VT*>(P.r);
 #pragma unroll
     for (int q = 0; q < QT; q++) {
         const int64_t e = r * Q + q;
         if (q >= Q) break;
         if (ph == P_PRE_A) {
-            if (S[q].pending) {  // the last iteration's step (alpha, omega still hold its values)
+            VT rn = (VT)0;
+            if (S[q].pending) {
+                // the last iteration's step (alpha, omega still hold its values): its
+                // residual r = s - omega t and its iterate x += alpha ph + omega sh
+                const VT om = (VT)S[q].omega;
+                rn = static_cast<const VT*>(P.s)[e] - om * static_cast<const VT*>(P.t)[e];
+                rv[e] = rn;
                 VT* X = static_cast<VT*>(P.x);
-                X[e] = X[e] + (VT)S[q].alpha * static_cast<const VT*>(P.ph)[e] +
-                       (VT)S[q].omega * static_cast<const VT*>(P.sh)[e];
+                X[e] = X[e] + (VT)S[q].alpha * static_cast<const VT*>(P.ph)[e] + om * static_cast<const VT*>(P.sh)[e];
             }
             if (MIXED && restart[q] && S[q].outer > 0 && !S[q].discard)
                 P.u[e] += S[q].scale * (double)static_cast<const VT*>(S[q].fold_best ? P.xb : P.x)[e];
             if (inner[q]) {
-                const VT nv = rv[e] + (VT)S[q].beta * (pv[e] - (VT)S[q].omega * vv[e]);
+                if (!S[q].pending) rn = rv[e];
+                const VT nv = rn + (VT)S[q].beta * (pv[e] - (VT)S[q].omega * vv[e]);
                 pv[e] = nv;
                 P.vy[0][e] = d0 * (float)nv;
             }
@@ -498,11 +596,12 @@ __device__ __forceinline__ void amg_pre_row(const Prob& P, int64_t r, int ph, co
     }
 }
 
-// A: v = A ph, B: t = A sh, from the staged slice (every lane of the warp calls).
+// A: v = A ph and (rh, v); B: t = A sh and (t, s), (t, t), (rh, s), (rh, t),
+// (s, s); from the staged slice (every lane of the warp calls).
 template <bool MIXED, int QT, typename Landed>
 __device__ __forceinline__ void amg_spmv_row(const Prob& P, int64_t r, bool valid, int ph, const RhsState* S,
-                                             const bool (&on)[QT], F2 (&af)[kChan][QT], double (&ad)[kChan][QT],
-                                             const int* colS,
+                                             const bool (&on)[QT], F2 (&af)[kChanAmg][QT],
+                                             double (&ad)[kChanAmg][QT], const int* colS,
                                              const typename std::conditional<MIXED, float, double>::type* valS,
                                              Landed&& landed) {
     using VT = typename std::conditional<MIXED, float, double>::type;
@@ -538,10 +637,10 @@ __device__ __forceinline__ void amg_spmv_row(const Prob& P, int64_t r, bool vali
         const int64_t e = r * Q + q;
         const VT lx = MIXED ? acc[q] : acc[q] + w0 * si[q];
         const VT res = sig * si[q] - lx;
+        const VT rhv = static_cast<const VT*>(P.rh)[e];
         if (ph == P_A) {
             static_cast<VT*>(P.v[0])[e] = res;
             if (MIXED && S[q].best_flag) static_cast<VT*>(P.xb)[e] = static_cast<const VT*>(P.x)[e];
-            const VT rhv = static_cast<const VT*>(P.rh)[e];
             if (MIXED) f2_add_prod(af[0][q], (float)rhv, (float)res);
             else ad[0][q] += (double)(rhv * res);
         } else {
@@ -550,36 +649,16 @@ __device__ __forceinline__ void amg_spmv_row(const Prob& P, int64_t r, bool vali
             if (MIXED) {
                 f2_add_prod(af[0][q], (float)res, (float)sv);
                 f2_add_prod(af[1][q], (float)res, (float)res);
+                f2_add_prod(af[2][q], (float)rhv, (float)sv);
+                f2_add_prod(af[3][q], (float)rhv, (float)res);
+                f2_add_prod(af[4][q], (float)sv, (float)sv);
             } else {
                 ad[0][q] += (double)(res * sv);
                 ad[1][q] += (double)(res * res);
+                ad[2][q] += (double)(rhv * sv);
+                ad[3][q] += (double)(rhv * res);
+                ad[4][q] += (double)(sv * sv);
             }
-        }
-    }
-}
-
-// C: r = s - omega t, and (rh, r), (r, r).  The step's x += alpha ph + omega sh
-// waits for the next PRE_A, which applies it only if the residual stayed finite
-// (so a breakdown never reaches x, which is u itself in the FP64 flow).
-template <bool MIXED, int QT>
-__device__ __forceinline__ void amg_c_row(const Prob& P, int64_t r, const RhsState* S, const bool (&inner)[QT],
-                                          F2 (&af)[kChan][QT], double (&ad)[kChan][QT]) {
-    using VT = typename std::conditional<MIXED, float, double>::type;
-    const int Q = P.Q;
-#pragma unroll
-    for (int q = 0; q < QT; q++) {
-        if (!inner[q]) continue;
-        const int64_t e = r * Q + q;
-        const VT om = (VT)S[q].omega;
-        const VT rn = static_cast<const VT*>(P.s)[e] - om * static_cast<const VT*>(P.t)[e];
-        static_cast<VT*>(P.r)[e] = rn;
-        const VT rhv = static_cast<const VT*>(P.rh)[e];
-        if (MIXED) {
-            f2_add_prod(af[0][q], (float)rhv, (float)rn);
-            f2_add_prod(af[1][q], (float)rn, (float)rn);
-        } else {
-            ad[0][q] += (double)(rhv * rn);
-            ad[1][q] += (double)(rn * rn);
         }
     }
 }
@@ -587,18 +666,30 @@ __device__ __forceinline__ void amg_c_row(const Prob& P, int64_t r, const RhsSta
 // ------------------------------------------------------------------------------
 // State transitions (run by the block that finishes a request's phase)
 // ------------------------------------------------------------------------------
-template <bool MIXED>
-__device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, const Ctl& ctl) {
+// c[] holds the step's reduced channels for this right-hand side.  The step
+// that ends an iteration is C in the row-scaled flows and B in the multigrid
+// flow, whose B also yields the new residual's (rh, r) and (r, r).
+template <bool MIXED, bool AMG>
+__device__ void advance(const Prob& P, int ph, RhsState& T, const double* c, const Ctl& ctl) {
+    const int ph_end = AMG ? P_B : P_C;
     if (ph == P_A) T.pending = 0;  // applied by PRE_A of this iteration
     switch (T.mode) {
         case M_INNER:
             if (ph == P_A) {
+                const double a = c[0];
                 if (MIXED) T.pp ^= 1;
                 if (!(fabs(a) > 0.0) || !isfinite(a)) T.mode = M_SKIP;
                 else T.alpha = T.rho / a;
-            } else if (ph == P_B) {
-                T.omega = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
-            } else if (ph == P_C) {
+            } else if (ph == P_B || ph == P_C) {
+                double a = c[0], b = c[1];  // C: (rh, r) and (r, r)
+                if (ph == P_B) {
+                    T.omega = (b > 0.0 && isfinite(a) && isfinite(b)) ? a / b : 0.0;
+                    if (!AMG) break;
+                    const double om = T.omega, ts = a, tt = b;
+                    a = c[2] - om * c[3];
+                    b = c[4] - 2.0 * om * ts + om * om * tt;
+                    if (b < 0.0) b = 0.0;  // rounding of a near-cancellation
+                }
                 T.iters++;
                 T.inner_iters++;
                 const double rn = sqrt(b);
@@ -636,7 +727,7 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
             }
             break;
         case M_SKIP:
-            if (ph == P_C) {
+            if (ph == ph_end) {
                 T.mode = M_RESTART;
                 T.discard = 0;
                 atomicAdd(ctl.nrestart, 1);
@@ -644,6 +735,7 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
             break;
         case M_RESTART:
             if (ph == P_A) {
+                const double a = c[0], b = c[1];
                 if (T.fnorm < 0) {
                     const double fn = sqrt(b);
                     T.fnorm = fn > 0 ? fn : 1.0;
@@ -672,7 +764,8 @@ __device__ void advance(const Prob& P, int ph, RhsState& T, double a, double b, 
                     atomicSub(ctl.active, 1);
                     atomicSub(ctl.nrestart, 1);
                 }
-            } else if (ph == P_C) {
+            } else if (ph == ph_end) {
+                const double a = c[0];
                 const double rn = sqrt(a);
                 T.rho = a;
                 T.alpha = 1.0;
@@ -713,7 +806,17 @@ struct ReqTable {
     ChunkTable lvl[kAmgMaxLevels]; // [l], 1 <= l < mlev: kThreads / amg_group(n_l)-row units of level l
     ChunkTable coarse;             // 8-row groups (a warp each) of every coarsest level
     int mlev;                      // largest (levels - 1) among the requests
+    int nreq;                      // requests in the launch (1: every unit is request 0's, no lookups)
+    int G[kAmgMaxLevels];          // [l], l >= 1: amg_group of the launch's rows at level l (see amg_lanes)
 };
+
+// Request of unit c of table T, and the unit's place in that request.
+__device__ __forceinline__ int unit_req(const ReqTable& tab, const ChunkTable& T, int c) {
+    return tab.nreq == 1 ? 0 : T.chunk_req[c];
+}
+__device__ __forceinline__ int unit_base(const ReqTable& tab, const ChunkTable& T, int ri) {
+    return tab.nreq == 1 ? 0 : T.chunk_base[ri];
+}
 
 template <typename VT>
 __host__ __device__ constexpr size_t stage_bytes_per_warp(int kmax) {
@@ -729,10 +832,12 @@ __host__ __device__ constexpr size_t stage_bytes_per_warp(int kmax) {
 // order; then a butterfly over the warp and a pairwise tree over the 8 warps.
 // The dependent chain is log-depth (FP64 additions have a long latency here)
 // and costs one L2 round trip a batch.
-template <bool MIXED, int QT>
+template <bool MIXED, int QT, bool AMG>
 __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int slot, int cnt, const RhsState* S,
-                                                    double (&fin)[kThreads / 32][kChan * QT],
-                                                    double (&tot)[kChan * QT], int* last, const Ctl& ctl) {
+                                                    double (&fin)[kThreads / 32][chan_count(AMG) * QT],
+                                                    double (&tot)[chan_count(AMG) * QT], int* last, const Ctl& ctl) {
+    constexpr int NC = chan_count(AMG);
+    const int nch = (AMG && ph == P_B) ? kChanAmg : kChan;  // the channels this step reduces
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the block's partial stores precede the barrier; thread 0's fence releases
     // them (cumulatively) with the arrival, and on the last arrival its second
@@ -746,42 +851,58 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
     }
     __syncthreads();
     if (*last) {
-        constexpr int kFinBatch = 16;
+        constexpr int kFinBatch = QT == 1 ? 16 : 8;
         const int nchunk = P.nchunk, Q = P.Q;
+        // two channels (or right-hand sides) at a time: 2 x kFinBatch loads in flight
 #pragma unroll
-        for (int e = 0; e < kChan * QT; e++) {
-            const int ch = e / QT, q = e % QT;
-            double acc = 0.0;
-            if (q < Q) {
-                const double* base = &P.part[((int64_t)slot * kChan + ch) * nchunk * Q + q];
+        for (int e0 = 0; e0 < NC * QT; e0 += 2) {
+            const int e1 = e0 + 1;
+            const bool on0 = e0 / QT < nch && e0 % QT < Q;                   // step-uniform
+            const bool on1 = e1 < NC * QT && e1 / QT < nch && e1 % QT < Q;  // step-uniform
+            double acc0 = 0.0, acc1 = 0.0;
+            if (on0 || on1) {
+                const double* b0 = &P.part[((int64_t)slot * NC + e0 / QT) * nchunk * Q + e0 % QT];
+                const double* b1 = &P.part[((int64_t)slot * NC + e1 / QT) * nchunk * Q + e1 % QT];
                 for (int l0 = tid; l0 < nchunk; l0 += kThreads * kFinBatch) {
-                    double v[kFinBatch];
+                    double v0[kFinBatch], v1[kFinBatch];
 #pragma unroll
                     for (int u = 0; u < kFinBatch; u++) {
                         const int l = l0 + u * kThreads;
-                        v[u] = l < nchunk ? __ldcg(base + (int64_t)l * Q) : 0.0;
+                        v0[u] = on0 && l < nchunk ? __ldcg(b0 + (int64_t)l * Q) : 0.0;
+                        v1[u] = on1 && l < nchunk ? __ldcg(b1 + (int64_t)l * Q) : 0.0;
                     }
 #pragma unroll
                     for (int w = 1; w < kFinBatch; w <<= 1)
 #pragma unroll
-                        for (int u = 0; u < kFinBatch; u += 2 * w) v[u] += v[u + w];
-                    acc += v[0];
+                        for (int u = 0; u < kFinBatch; u += 2 * w) {
+                            v0[u] += v0[u + w];
+                            v1[u] += v1[u + w];
+                        }
+                    acc0 += v0[0];
+                    acc1 += v1[0];
                 }
             }
-            acc = warp_sum(acc);
-            if (lane == 0) fin[wid][e] = acc;
+            if (on0) acc0 = warp_sum(acc0);
+            if (on1) acc1 = warp_sum(acc1);
+            if (lane == 0) {
+                fin[wid][e0] = acc0;
+                if (e1 < NC * QT) fin[wid][e1] = acc1;
+            }
         }
         __syncthreads();
         static_assert(kThreads / 32 == 8, "the warp tree below sums 8 warps");
-        if (tid < kChan * QT) {
+        if (tid < NC * QT) {
             const double* f = &fin[0][tid];
-            constexpr int W = kChan * QT;
+            constexpr int W = NC * QT;
             tot[tid] = ((f[0] + f[W]) + (f[2 * W] + f[3 * W])) + ((f[4 * W] + f[5 * W]) + (f[6 * W] + f[7 * W]));
         }
         __syncthreads();
         if (tid < P.Q) {
             RhsState T = S[tid];
-            advance<MIXED>(P, ph, T, tot[0 * QT + tid], tot[1 * QT + tid], ctl);
+            double cv[NC];
+#pragma unroll
+            for (int ch = 0; ch < NC; ch++) cv[ch] = tot[ch * QT + tid];
+            advance<MIXED, AMG>(P, ph, T, cv, ctl);
             P.st[tid] = T;
         }
         // the grid barrier that ends this phase releases the new states and the
@@ -797,10 +918,11 @@ enum VStep : int { V_DOWN = 0, V_COARSE = 1, V_UP = 2 };
 // request ri's and this warp's slice of it holds rows (its slice in *slice2);
 // else -1.  Such a tile is staged exactly like tile c, so its slice can be
 // requested ahead.
-__device__ __forceinline__ int next_tile(const ChunkTable& T, int c, int ri, int64_t nrows, int wid, int64_t& slice2) {
+__device__ __forceinline__ int next_tile(const ReqTable& tab, const ChunkTable& T, int c, int ri, int64_t nrows,
+                                         int wid, int64_t& slice2) {
     const int c2 = c + (int)gridDim.x;
-    if (c2 >= T.nchunks || T.chunk_req[c2] != ri) return -1;
-    slice2 = (int64_t)(c2 - T.chunk_base[ri]) * (kCh / kSlice) + wid;
+    if (c2 >= T.nchunks || unit_req(tab, T, c2) != ri) return -1;
+    slice2 = (int64_t)(c2 - unit_base(tab, T, ri)) * (kCh / kSlice) + wid;
     return slice2 * kSlice < nrows ? c2 : -1;
 }
 
@@ -810,14 +932,19 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     using VT = typename std::conditional<MIXED, float, double>::type;
     extern __shared__ __align__(16) unsigned char stage_smem[];
     __shared__ RhsState S[QT];
+    __shared__ __align__(16) Prob sP;
+    __shared__ __align__(16) AmgHeader sH;
+    static_assert(sizeof(Prob) % 8 == 0 && sizeof(AmgHeader) % 8 == 0, "descriptors are copied in 8-byte words");
     // per-warp partials of the block's pending tiles, summed into tile partials
     // (in warp order) only when kRedTiles are pending or the request changes:
     // the warps of a block do not wait for each other tile by tile
-    constexpr int kRedTiles = QT <= 2 ? 16 : (QT == 4 ? 8 : 4);
-    __shared__ double red[kRedTiles][kThreads / 32][kChan * QT];
+    constexpr int NC = chan_count(AMG);
+    // about 5 KB of pending partials at most
+    constexpr int kRedTiles = 80 / (NC * QT) > 16 ? 16 : (80 / (NC * QT) < 2 ? 2 : 80 / (NC * QT));
+    __shared__ double red[kRedTiles][kThreads / 32][NC * QT];
     __shared__ int red_lc[kRedTiles];
-    __shared__ double fin[kThreads / 32][kChan * QT];
-    __shared__ double tot[kChan * QT];
+    __shared__ double fin[kThreads / 32][NC * QT];
+    __shared__ double tot[NC * QT];
     __shared__ int last;
     __shared__ float vagg[kThreads / kAmgAgg];  // a block's row residuals on a small level (agg_sum)
     __shared__ __align__(8) uint64_t stage_bar[kThreads / 32][2];
@@ -849,11 +976,36 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     // the request whose state S holds, while no phase has advanced it since
     int held = -1;
     unsigned bar_epoch = 0;  // grid barriers passed (the same count in every block)
+    // The descriptor (and multigrid header) of the request the block works on,
+    // copied into shared memory when the request changes.  Each grid barrier's
+    // acquire leaves none of them in L1, so read from global memory every step
+    // would start with a chain of dependent L2 round trips (table -> descriptor
+    // -> header -> level arrays) before the first row is touched.  Neither is
+    // written while the solver runs.
+    int desc = -1;
+    auto load_desc = [&](int ri) {
+        if (ri == desc) return;
+        __syncthreads();  // every thread is done with the previous one
+        const unsigned long long* gp = reinterpret_cast<const unsigned long long*>(tab.prob[ri]);
+        for (int w = tid; w < (int)(sizeof(Prob) / 8); w += kThreads)
+            reinterpret_cast<unsigned long long*>(&sP)[w] = __ldcg(gp + w);
+        __syncthreads();
+        if (AMG && sP.amg != nullptr) {
+            const unsigned long long* gh = reinterpret_cast<const unsigned long long*>(sP.amg);
+            for (int w = tid; w < (int)(sizeof(AmgHeader) / 8); w += kThreads)
+                reinterpret_cast<unsigned long long*>(&sH)[w] = __ldcg(gh + w);
+            __syncthreads();
+            if (tid == 0) sP.amg = &sH;
+            __syncthreads();
+        }
+        desc = ri;
+    };
     // Loads request ri's per-RHS state into S (block-wide) and its masks.
     auto enter = [&](int ri, int ph) {
         held = ri;
+        load_desc(ri);
         __syncthreads();
-        const Prob& P = *tab.prob[ri];
+        const Prob& P = sP;
         // a K above the one the staging buffers were sized for (a wrong K in the
         // request list) would overrun shared memory, and a hierarchy of another
         // operator would be read out of bounds: do no work and end the launch
@@ -885,30 +1037,36 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     };
 
     // One Krylov phase over every request's level-0 tiles, then the grid barrier.
+    // the step that ends an iteration: it restarts the Krylov vectors of the
+    // right-hand sides in RESTART and its barrier precedes the exit test
+    constexpr int ph_end = AMG ? P_B : P_C;
     auto fine_phase = [&](int ph) -> bool {
         const bool reduce = ph == P_A || ph == P_B || ph == P_C;
+        const int nch = (AMG && ph == P_B) ? kChanAmg : kChan;  // the channels this step reduces
         const int slot = red_slot(ph);
         int cur = -1, tiles = 0, nred = 0;
-        // tile partials of the pending tiles of request P: each the sum of its 8 warp partials in order
+        // tile partials of the pending tiles of request P: each the sum of its 8 warp partials (a pairwise tree)
         auto flush = [&](const Prob& P) {
             __syncthreads();
-            for (int e = tid; e < nred * kChan * QT; e += kThreads) {
-                const int t = e / (kChan * QT), j = e % (kChan * QT);
-                double v = 0.0;
-                for (int w = 0; w < kThreads / 32; w++) v += red[t][w][j];
+            for (int e = tid; e < nred * NC * QT; e += kThreads) {
+                const int t = e / (NC * QT), j = e % (NC * QT);
+                if (j / QT >= nch) continue;
+                const double* rw = &red[t][0][j];
+                constexpr int W = NC * QT;  // stride between warps
+                const double v = ((rw[0] + rw[W]) + (rw[2 * W] + rw[3 * W])) + ((rw[4 * W] + rw[5 * W]) + (rw[6 * W] + rw[7 * W]));
                 const int ch = j / QT, q = j % QT;
-                if (q < P.Q) P.part[(((int64_t)slot * kChan + ch) * P.nchunk + red_lc[t]) * P.Q + q] = v;
+                if (q < P.Q) P.part[(((int64_t)slot * NC + ch) * P.nchunk + red_lc[t]) * P.Q + q] = v;
             }
             __syncthreads();
             nred = 0;
         };
         for (int c = blockIdx.x;; c += gridDim.x) {
-            const int ri = c < tab.fine.nchunks ? tab.fine.chunk_req[c] : -1;
+            const int ri = c < tab.fine.nchunks ? unit_req(tab, tab.fine, c) : -1;
             if (ri != cur) {
                 // leaving request `cur`: publish this block's tiles of it
                 if (cur >= 0 && reduce && tiles > 0) {
-                    flush(*tab.prob[cur]);
-                    arrive_and_finalize<MIXED, QT>(*tab.prob[cur], ph, slot, tiles, S, fin, tot, &last, ctl);
+                    flush(sP);  // still request cur's descriptor
+                    arrive_and_finalize<MIXED, QT, AMG>(sP, ph, slot, tiles, S, fin, tot, &last, ctl);
                 }
                 if (ri < 0) break;
                 cur = ri;
@@ -916,21 +1074,21 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 enter(ri, ph);
             }
             if (all_done) continue;  // the whole request is finished: no work, no arrival
-            const Prob& P = *tab.prob[ri];
-            const int lc = c - tab.fine.chunk_base[ri];
+            const Prob& P = sP;
+            const int lc = c - unit_base(tab, tab.fine, ri);
             const int64_t r = (int64_t)lc * kCh + tid;
             const int64_t slice = (int64_t)lc * (kCh / kSlice) + wid;
-            F2 af[kChan][QT];
-            double ad[kChan][QT];
+            F2 af[NC][QT];
+            double ad[NC][QT];
 #pragma unroll
-            for (int ch = 0; ch < kChan; ch++)
+            for (int ch = 0; ch < NC; ch++)
 #pragma unroll
                 for (int q = 0; q < QT; q++) { af[ch][q].hi = 0.0f; af[ch][q].lo = 0.0f; ad[ch][q] = 0.0; }
             // warp-uniform: lane 0 stages the whole slice and every lane waits for it
             const bool staged = (ph == P_A || ph == P_B) && any_inner && slice * kSlice < P.n && st.ok;
             if (staged) {
                 int64_t slice2 = 0;
-                const int cn = next_tile(tab.fine, c, ri, P.n, wid, slice2);
+                const int cn = next_tile(tab, tab.fine, c, ri, P.n, wid, slice2);
                 // FP32 multigrid flow: the hierarchy's level-0 weights (the operator's hi
                 // values, copied at set-up), the array the V-cycle's level-0 steps read too
                 const void* vsrc = (AMG && MIXED) ? static_cast<const void*>(P.amg->lv[0].val) : P.val;
@@ -938,37 +1096,40 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 const int* colS = st.col(b);
                 const VT* valS = static_cast<const VT*>(st.val(b));
                 auto landed = [&]() { return st.wait(b, ctl.err); };
-                if (AMG) amg_spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, af, ad, colS, valS, landed);
+                if constexpr (AMG) amg_spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, af, ad, colS, valS, landed);
                 else spmv_row<MIXED, QT>(P, r, r < P.n, ph, S, inner, c1, c2, af, ad, colS, valS, landed);
             }
             if (r < P.n) {
-                // a restart computes its residual in A and resets the Krylov vectors in C,
-                // so that its first inner step starts at the next iteration's A
-                if (ph == P_A || ph == P_B) {
-                    if (any_restart && ph == P_A) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
-                } else if (ph == P_C) {
-                    if (any_inner) {
-                        if (AMG) amg_c_row<MIXED, QT>(P, r, S, inner, af, ad);
-                        else if (MIXED) elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
-                        else c_row_f64<QT>(P, r, S, inner, ad);
+                // a restart computes its residual in A and resets the Krylov vectors in
+                // the iteration's last step, so that its first inner step starts at the
+                // next iteration
+                if (ph == P_A) {
+                    if (any_restart) restart_row<MIXED, QT, NC>(P, r, ph, S, restart, ad);
+                } else if (ph == ph_end) {
+                    if constexpr (!AMG) {
+                        if (any_inner) {
+                            if (MIXED) elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
+                            else c_row_f64<QT>(P, r, S, inner, ad);
+                        }
                     }
-                    if (any_restart) restart_row<MIXED, QT>(P, r, ph, S, restart, ad);
-                } else {
-                    if (AMG) amg_pre_row<MIXED, QT>(P, r, ph, S, inner, restart);
+                    if (any_restart) restart_row<MIXED, QT, NC>(P, r, ph, S, restart, ad);
+                } else if (ph != P_B) {
+                    if constexpr (AMG) amg_pre_row<MIXED, QT>(P, r, ph, S, inner, restart);
                     else elementwise_row<MIXED, QT>(P, r, ph, S, inner, restart, af);
                 }
             }
             if (!reduce) continue;
             // tile partials in a fixed order: FP32 partials within the warp in FP32,
             // then (at the next flush) the 8 warps in order
-#pragma unroll
-            for (int ch = 0; ch < kChan; ch++)
-#pragma unroll
-                for (int q = 0; q < QT; q++) {
-                    double v = f2_to_double(warp_sum_f2(af[ch][q]));
-                    if (any_restart || !MIXED) v += warp_sum(ad[ch][q]);
-                    if (lane == 0) red[nred][wid][ch * QT + q] = v;
+            {
+                const bool with64 = any_restart || !MIXED;
+                if constexpr (AMG) {
+                    if (ph == P_B) tile_partials<MIXED, QT, NC, kChanAmg>(af, ad, with64, lane, red[nred][wid]);
+                    else tile_partials<MIXED, QT, NC, kChan>(af, ad, with64, lane, red[nred][wid]);
+                } else {
+                    tile_partials<MIXED, QT, NC, kChan>(af, ad, with64, lane, red[nred][wid]);
                 }
+            }
             if (tid == 0) red_lc[nred] = lc;
             nred++;
             tiles++;
@@ -976,7 +1137,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         }
         // the stop word is written only before the last barrier of an iteration and
         // read only after it, so every block takes the same exit decision
-        if (ph == P_C && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
+        if (ph == ph_end && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
             *ctl.stop = 1;
         if (reduce) held = -1;  // the states were advanced at the arrivals
         const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit,
@@ -991,19 +1152,19 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         const ChunkTable& T = kind == V_COARSE ? tab.coarse : (l == 0 ? tab.fine : tab.lvl[l]);
         int cur = -1;
         for (int c = blockIdx.x; c < T.nchunks; c += gridDim.x) {
-            const int ri = T.chunk_req[c];
+            const int ri = unit_req(tab, T, c);
             if (ri != cur) {
                 cur = ri;
                 // V-cycle steps leave the states alone: the one loaded by the
                 // preceding PRE phase (or step) stays valid
                 if (ri != held) enter(ri, P_PRE_A);
             }
-            const Prob& P = *tab.prob[ri];
+            const Prob& P = sP;
             const int m = P.amg_levels - 1;  // the request's coarsest level
             if (!any_inner || (kind != V_COARSE && l >= m)) continue;
             const AmgHeader& H = *P.amg;
             const int Q = P.Q;
-            const int lc = c - T.chunk_base[ri];
+            const int lc = c - unit_base(tab, T, ri);
             const VT* B0 = static_cast<const VT*>(side == 0 ? P.p[0] : P.s);
             VT* X0 = static_cast<VT*>(side == 0 ? P.ph : P.sh);
             if (kind == V_COARSE) {
@@ -1024,7 +1185,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             }
             const int64_t nl = H.lv[l].n;
             // level 0: a lane per row (staged slices); level >= 1: G lanes per row
-            const int G = l == 0 ? 1 : amg_group(nl);
+            const int G = l == 0 ? 1 : amg_lanes(tab.G[l], nl, QT);
             const int64_t r = (int64_t)lc * (kThreads / G) + tid / G;
             const bool valid = r < nl;
             // whole warps past the level's end have nothing to do, except in a down
@@ -1039,7 +1200,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                 if (!st.ok) continue;
                 const int64_t slice = (int64_t)lc * (kCh / kSlice) + wid;
                 int64_t slice2 = 0;
-                const int cn = next_tile(tab.fine, c, ri, nl, wid, slice2);
+                const int cn = next_tile(tab, tab.fine, c, ri, nl, wid, slice2);
                 b = st.acquire(c, slice, cn, slice2, P.col, H.lv[0].val, 4, P.k, ctl.err);
                 colS = st.col(b);
                 w0S = static_cast<const float*>(st.val(b));
@@ -1072,11 +1233,14 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                         if (inner[q]) vdown_finish(H, 0, 1, r, valid, Q, q, bi[q] - ay[q], P.vr[0], P.vb[1], Yn, vagg);
                     continue;
                 }
+                // level >= 1: every right-hand side in one pass over the row's entries
+                float ay[QT];
+                al_rows<QT>(H.lv[l], r, valid, G, yi, [&](int64_t j, float (&x)[QT]) { load_row<QT>(Y, j, Q, x); },
+                            ay);
 #pragma unroll
                 for (int q = 0; q < QT; q++) {
                     if (!inner[q]) continue;  // block-uniform
-                    vdown_row(H, l, G, r, valid, Q, q, bi[q], yi[q], [&](int64_t j) { return Y[j * Q + q]; },
-                              P.vr[l], P.vb[l + 1], Yn, a0, vagg);
+                    vdown_finish(H, l, G, r, valid, Q, q, bi[q] - ay[q], P.vr[l], P.vb[l + 1], Yn, vagg);
                 }
             } else {
                 const float* Xc = P.vx[l + 1];
@@ -1100,16 +1264,18 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
                     continue;
                 }
                 if (!valid && G == 1) continue;
+                // level >= 1: x = y + x_c + d (r - A_l P x_c), every right-hand side in one pass
+                float xc[QT], apx[QT];
 #pragma unroll
-                for (int q = 0; q < QT; q++) {
-                    if (!inner[q]) continue;
-                    const int64_t e = r * Q + q;
-                    const float x = vup_row(H, l, G, r, valid, yi[q], rr[q],
-                                            [&](int64_t J) { return Xc[J * Q + q]; }, a0);
-                    if (!valid || (lane & (G - 1)) != 0) continue;
-                    if (l == 0) X0[e] = (VT)x;
-                    else P.vx[l][e] = x;
-                }
+                for (int q = 0; q < QT; q++) xc[q] = 0.0f;
+                if (valid) load_row<QT>(Xc, r / kAmgAgg, Q, xc);
+                al_rows<QT>(H.lv[l], r, valid, G, xc,
+                            [&](int64_t j, float (&x)[QT]) { load_row<QT>(Xc, j / kAmgAgg, Q, x); }, apx);
+                if (!valid || (lane & (G - 1)) != 0) continue;
+                const float dl = H.lv[l].dinv[r];
+#pragma unroll
+                for (int q = 0; q < QT; q++)
+                    if (inner[q]) P.vx[l][r * Q + q] = yi[q] + xc[q] + dl * (rr[q] - apx[q]);
             }
         }
         const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit,
@@ -1130,7 +1296,7 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         bool ok = true;
         if (AMG) {
             ok = fine_phase(P_PRE_A) && vcycle(0) && fine_phase(P_A) && fine_phase(P_PRE_B) && vcycle(1) &&
-                 fine_phase(P_B) && fine_phase(P_C);
+                 fine_phase(P_B);
         } else {
             // read after the last barrier of the previous iteration: identical in every block
             const bool pre_a = !MIXED || *(volatile int*)ctl.nrestart > 0;
@@ -1178,7 +1344,7 @@ ReqLayout req_layout(void* ws, int64_t n, int Q, int prec, int precond) {
     const size_t vt = prec == MVGD_FP64 ? sizeof(double) : sizeof(float);
     L.prob = cv.take<Prob>(1);
     L.st = cv.take<RhsState>(Q);
-    L.part = cv.take<double>(kRedSlots * kChan * nchunk * Q);
+    L.part = cv.take<double>(kRedSlots * chan_count(precond == 2) * nchunk * Q);
     L.arrive = cv.take<unsigned>(kRedSlots);
     L.info = cv.take<mvgd_solve_info>(Q);
     L.fs = cv.take<double>(n * Q);
@@ -1571,6 +1737,17 @@ MVGD_API mvgd_status mvgd_iterate(const mvgd_request* reqs, int32_t count, int32
     memset(&tab, 0, sizeof(tab));
     tab.prob = C.prob;
     tab.mlev = mlev;
+    tab.nreq = count;
+    const int qt = maxQ <= 1 ? 1 : (maxQ <= 2 ? 2 : (maxQ <= 4 ? 4 : 8));  // the solver's right-hand-side width
+    for (int l = 0; l < kAmgMaxLevels; l++) {
+        int64_t rows = 0;
+        for (int i = 0; amg && l > 0 && i < count; i++) {
+            int64_t sizes[kAmgMaxLevels];
+            const int nl = amg_levels(reqs[i].n, sizes);
+            if (l < nl - 1) rows += sizes[l];
+        }
+        tab.G[l] = l == 0 || rows == 0 ? 1 : amg_group(rows);
+    }
     // table t: 0 = level-0 tiles, 1 .. mlev-1 = level-t tiles, kAmgMaxLevels = coarsest rows by 8
     for (int t = 0; t <= kAmgMaxLevels; t++) {
         const bool coarse = t == kAmgMaxLevels;
@@ -1588,7 +1765,7 @@ MVGD_API mvgd_status mvgd_iterate(const mvgd_request* reqs, int32_t count, int32
                 if (t == 0) A.nchunk[i] = (int)((R.n + kCh - 1) / kCh);
                 else if (coarse) A.nchunk[i] = (int)((sizes[nl - 1] + kThreads / kWarp - 1) / (kThreads / kWarp));
                 else if (t < nl - 1) {
-                    const int64_t rows = kThreads / amg_group(sizes[t]);  // rows per unit
+                    const int64_t rows = kThreads / amg_lanes(tab.G[t], sizes[t], qt);  // rows per unit
                     A.nchunk[i] = (int)((sizes[t] + rows - 1) / rows);
                 } else {
                     A.nchunk[i] = 0;

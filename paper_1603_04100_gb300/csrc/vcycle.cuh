@@ -116,23 +116,87 @@ __device__ __forceinline__ void a0_rows_staged(const int* colS, const float* w, 
 }
 
 // Level-l (>= 1) product with the explicit Galerkin matrix, row r taken by the
-// G lanes of its group (G a power of two <= 32, groups aligned in the warp):
-// lane `sub` sums slots sub, sub + G, ... and the group adds its partials by a
-// butterfly, so every lane of the group returns the same value.  Padding slots
-// are (own row, 0), so every lane runs to the slice's widest row.  Lanes of
-// invalid rows return 0 but take part in the shuffles.
+// G lanes of its group (groups aligned in the warp).  The sum is split over
+// V = amg_group(n_l) virtual lanes (V a multiple of G, M = V / G <= 8 of them a
+// lane): virtual lane v adds the row's slots v, v + V, v + 2V, ... in order,
+// and a butterfly over the V virtual lanes (offsets 1, 2, 4, ...) adds them.
+// Lane j of the group holds virtual lanes j, j + G, ...; the butterfly's
+// offsets below G are shuffles, the others adds inside the lane -- the same
+// operations in the same order for every G, so the result depends on V (the
+// request's level size) alone, and every lane of the group returns it.
+// Padding slots are (own row, 0).  Lanes of invalid rows return 0 but take
+// part in the shuffles.
+template <int M, int QT, typename XR>
+__device__ __forceinline__ void al_rows_m(const AmgLevel& Lv, int64_t r, bool valid, int G, const float (&xi)[QT],
+                                          XR&& xrow, float (&out)[QT]) {
+    const int V = M * G;
+    float acc[M][QT];
+#pragma unroll
+    for (int m = 0; m < M; m++)
+#pragma unroll
+        for (int q = 0; q < QT; q++) acc[m][q] = 0.0f;
+    if (valid) {
+        const int j = (int)(lane_id() & (G - 1));
+        const int64_t base = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
+        // the slice's widest row, rounded up to whole groups of V slots: every row
+        // is padded with (own row, 0) to the full stride, whose terms add exact zeros
+        const int w = (Lv.sw[r / kSlice] + V - 1) & ~(V - 1);
+        constexpr int kUnroll = M >= 4 ? 1 : 4 / M;  // about four slots in flight a lane
+#pragma unroll kUnroll
+        for (int s0 = 0; s0 < w; s0 += V) {
+#pragma unroll
+            for (int m = 0; m < M; m++) {
+                const int64_t e = base + (int64_t)(s0 + j + m * G) * kSlice;
+                const float a = Lv.val[e];
+                float x[QT];
+                xrow((int64_t)Lv.col[e], x);  // every right-hand side of the neighbour at once
+#pragma unroll
+                for (int q = 0; q < QT; q++) acc[m][q] = fmaf(a, x[q] - xi[q], acc[m][q]);
+            }
+        }
+    }
+    for (int o = 1; o < G; o <<= 1)
+#pragma unroll
+        for (int m = 0; m < M; m++)
+#pragma unroll
+            for (int q = 0; q < QT; q++) acc[m][q] += __shfl_xor_sync(0xffffffffu, acc[m][q], o);
+#pragma unroll
+    for (int d = 1; d < M; d <<= 1)
+#pragma unroll
+        for (int m = 0; m < M; m++)
+            if ((m & d) == 0)
+#pragma unroll
+                for (int q = 0; q < QT; q++) {
+                    const float t = acc[m][q] + acc[m + d][q];
+                    acc[m][q] = t;
+                    acc[m + d][q] = t;
+                }
+    const float rs = valid ? Lv.rs[r] : 0.0f;
+#pragma unroll
+    for (int q = 0; q < QT; q++) out[q] = valid ? fmaf(rs, xi[q], acc[0][q]) : 0.0f;
+}
+
+// Products of every right-hand side at once: out[q] = (A_l x_q)[r], the
+// neighbours' rows read by `xrow(j, x)`; each q's operations are those of a
+// single product, in the same order.
+template <int QT, typename XR>
+__device__ __forceinline__ void al_rows(const AmgLevel& Lv, int64_t r, bool valid, int G, const float (&xi)[QT],
+                                        XR&& xrow, float (&out)[QT]) {
+    // M = V / G <= kAmgMaxPerLane / QT (amg_lanes): no larger case is instantiated
+    constexpr int kMmax = kAmgMaxPerLane / QT > 1 ? kAmgMaxPerLane / QT : 1;
+    const int M = amg_group(Lv.n) / G;  // warp-uniform
+    if (kMmax >= 8 && M >= 8) al_rows_m<(kMmax >= 8 ? 8 : 1), QT>(Lv, r, valid, G, xi, xrow, out);
+    else if (kMmax >= 4 && M >= 4) al_rows_m<(kMmax >= 4 ? 4 : 1), QT>(Lv, r, valid, G, xi, xrow, out);
+    else if (kMmax >= 2 && M >= 2) al_rows_m<(kMmax >= 2 ? 2 : 1), QT>(Lv, r, valid, G, xi, xrow, out);
+    else al_rows_m<1, QT>(Lv, r, valid, G, xi, xrow, out);
+}
+
 template <typename XV>
 __device__ __forceinline__ float al_row(const AmgLevel& Lv, int64_t r, bool valid, int G, float xi, XV&& xv) {
-    float acc = 0.0f;
-    if (valid) {
-        const int64_t base = (r / kSlice) * (int64_t)(kSlice * kAmgStride) + (r % kSlice);
-        const int w = Lv.sw[r / kSlice];
-#pragma unroll 4
-        for (int s = (int)(lane_id() & (G - 1)); s < w; s += G)
-            acc = fmaf(Lv.val[base + s * kSlice], xv((int64_t)Lv.col[base + s * kSlice]) - xi, acc);
-    }
-    for (int o = 1; o < G; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return valid ? fmaf(Lv.rs[r], xi, acc) : 0.0f;
+    const float x1[1] = {xi};
+    float o1[1];
+    al_rows<1>(Lv, r, valid, G, x1, [&](int64_t j, float (&x)[1]) { x[0] = xv(j); }, o1);
+    return o1[0];
 }
 
 // Sum of a value over the 8 rows of each aggregate, rows of G lanes each,
