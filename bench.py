@@ -150,19 +150,20 @@ def solver_bytes_per_row(k: int, mixed: bool, iters: int, restarts: int, amg_coa
     Plain FP64, per iteration 24k + 160; per restart 12k + 96.
 
     Multigrid flow (amg_coarse = bytes per fine row of one V-cycle's levels >= 1,
-    including the coarsest solve), per iteration with V-cycle level 0 on FP32
+    including the coarsest solve), per iteration (six grid steps; the last
+    step's r = s - omega t is formed in PRE_A) with V-cycle level 0 on FP32
     weights:
       V-cycle level 0: down col 4k + val 4(k+1) + b,y 4+vt + write r + b,y of
         level 1 (1/8 each) 5; up col 4k + val 4(k+1) + y,r,d 12 + write x vt
         -> 16k + 29 + 2 vt (+ amg_coarse), twice per iteration
-      mixed (vt 4): PRE_A r,p,v,d 16 + p,y 8; A 8k+4 + ph,rh 8 + v 4;
-        PRE_B r,v,d 12 + s,y 8; B 8k+4 + sh,s 8 + t 4; C x,ph,sh,s,t,rh 24 + x,r 8;
-        two V-cycles 32k + 74                        -> 48k + 182 + 2 amg_coarse
-      FP64 (vt 8): PRE_A 40; A 12k+8 + 16 + 8; PRE_B 32; B 12k+8 + 16 + 8;
-        C 48 + 16; two V-cycles 32k + 90             -> 56k + 290 + 2 amg_coarse
+      mixed (vt 4): PRE_A s,t,x,ph,sh,p,v,d 32 + r,x,p,y 16; A 8k+4 + ph,rh 8 + v 4;
+        PRE_B r,v,d 12 + s,y 8; B 8k+4 + sh,s,rh 12 + t 4;
+        two V-cycles 32k + 74                        -> 48k + 178 + 2 amg_coarse
+      FP64 (vt 8): PRE_A 60 + 28; A 12k+8 + 16 + 8; PRE_B 20 + 12; B 12k+8 + 24 + 8;
+        two V-cycles 32k + 90                        -> 56k + 282 + 2 amg_coarse
     """
     if amg_coarse is not None:
-        per = (48 * k + 182) if mixed else (56 * k + 290)
+        per = (48 * k + 178) if mixed else (56 * k + 282)
         return iters * (per + 2 * amg_coarse) + restarts * ((12 * k + 92) if mixed else (12 * k + 96))
     if mixed:
         return iters * (16 * k + 80) + restarts * (12 * k + 92)

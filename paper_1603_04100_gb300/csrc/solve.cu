@@ -85,7 +85,7 @@ struct Prob {
     double* r64;
     void* invd;        // [n] VT: 1 / (sigma + sum_s |w_s|), the left scaling (precond == 1)
     RhsState* st;      // [Q]
-    double* part;      // [kRedSlots][kChan][nchunk][Q]
+    void* part;        // [kRedSlots][channels][nchunk][Q] tile partials (Part<MIXED>: F2 or double)
     unsigned* arrive;  // [kRedSlots]
     int nchunk, pad;
     // multigrid right preconditioning (precond == 2); amg == nullptr otherwise
@@ -253,12 +253,60 @@ __device__ __forceinline__ F2 warp_sum_f2_multi(F2 (&v)[E], int lane, int& chan)
 
 __host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
 
+// Tile partials and their sums: F2 (double-float on the FP32 pipe) in the
+// FP32 flow, double in the FP64 one.  One SM sums a request's thousands of
+// partials in each reducing step; GB300 issues FP64 additions at 2 lanes a
+// clock an SM (a warp instruction every 16 clocks, 63 clocks of latency), so in
+// FP64 that sum alone took about 1 us a channel at 1M rows, and F2 additions
+// (eight FP32 operations) take a fraction of it with about 48 bits.  The F2
+// range is FP32's: the FP32 flow's squared residual norms stay below 3.4e38
+// (||f|| below about 1.8e19) or the step reports a non-finite residual.
+template <bool MIXED>
+using Part = typename std::conditional<MIXED, F2, double>::type;
+__device__ __forceinline__ F2 part_add(F2 a, F2 b) { return f2_add(a, b); }
+__device__ __forceinline__ double part_add(double a, double b) { return a + b; }
+__device__ __forceinline__ double part_value(F2 a) { return f2_to_double(a); }
+__device__ __forceinline__ double part_value(double a) { return a; }
+template <typename PT>
+__device__ __forceinline__ PT part_zero() {
+    if constexpr (std::is_same<PT, F2>::value) {
+        F2 z;
+        z.hi = 0.0f;
+        z.lo = 0.0f;
+        return z;
+    } else {
+        return 0.0;
+    }
+}
+template <typename PT>
+__device__ __forceinline__ PT part_from(double x) {
+    if constexpr (std::is_same<PT, F2>::value) {
+        F2 z;
+        z.hi = __double2float_rn(x);
+        z.lo = __double2float_rn(x - (double)z.hi);
+        return z;
+    } else {
+        return x;
+    }
+}
+__device__ __forceinline__ F2 part_warp_sum(F2 v) { return warp_sum_f2(v); }
+__device__ __forceinline__ double part_warp_sum(double v) { return warp_sum(v); }
+__device__ __forceinline__ F2 part_load(const F2* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    F2 z;
+    z.hi = v.x;
+    z.lo = v.y;
+    return z;
+}
+__device__ __forceinline__ double part_load(const double* p) { return __ldcg(p); }
+
 // A warp's partials of its slice of a tile, channels 0 .. NCH-1 of every
 // right-hand side, into out[ch * QT + q]: the FP32 (F2) products summed over
 // the warp, plus the FP64 ones where there are any (`with64`).
 template <bool MIXED, int QT, int NC, int NCH>
 __device__ __forceinline__ void tile_partials(const F2 (&af)[NC][QT], const double (&ad)[NC][QT], bool with64,
-                                              int lane, double* out) {
+                                              int lane, Part<MIXED>* out) {
+    using PT = Part<MIXED>;
     constexpr int E = pow2_at_least(NCH * QT);
     double w64[NCH * QT];
 #pragma unroll
@@ -266,7 +314,8 @@ __device__ __forceinline__ void tile_partials(const F2 (&af)[NC][QT], const doub
     if constexpr (MIXED && E > 32) {  // more values than lanes: one butterfly each
 #pragma unroll
         for (int e = 0; e < NCH * QT; e++) {
-            const double x = f2_to_double(warp_sum_f2(af[e / QT][e % QT])) + w64[e];
+            F2 x = warp_sum_f2(af[e / QT][e % QT]);
+            if (with64) x = f2_add(x, part_from<F2>(w64[e]));
             if (lane == 0) out[e] = x;
         }
     } else if constexpr (MIXED) {
@@ -281,15 +330,19 @@ __device__ __forceinline__ void tile_partials(const F2 (&af)[NC][QT], const doub
         int chan;
         const F2 tot = warp_sum_f2_multi<E32>(v, lane, chan);
         if ((lane & (32 / E32 - 1)) == 0 && chan < NCH * QT) {
-            double x = f2_to_double(tot);
+            F2 x = tot;
+            if (with64) {
+                double w = 0.0;
 #pragma unroll
-            for (int e = 0; e < NCH * QT; e++)
-                if (e == chan) x += w64[e];
+                for (int e = 0; e < NCH * QT; e++)
+                    if (e == chan) w = w64[e];
+                x = f2_add(x, part_from<F2>(w));
+            }
             out[chan] = x;
         }
     } else if (lane == 0) {
 #pragma unroll
-        for (int e = 0; e < NCH * QT; e++) out[e] = w64[e];
+        for (int e = 0; e < NCH * QT; e++) out[e] = part_from<PT>(w64[e]);
     }
 }
 
@@ -596,6 +649,77 @@ __device__ __forceinline__ void amg_pre_row(const Prob& P, int64_t r, int ph, co
     }
 }
 
+// PRE_A / PRE_B of NT rows at once (rows r[k], k < n, of up to NT tiles of one
+// request; `ok[k]`: the row exists), for right-hand sides that are INNER or
+// have a pending step (no RESTART in the request: its fold goes row by row).
+// Every operand of every row is loaded before any is used, so a block's tiles
+// cost one memory round trip a group instead of one a tile; each row's
+// arithmetic is that of amg_pre_row.
+template <bool MIXED, int QT, int NT>
+__device__ __forceinline__ void amg_pre_rows(const Prob& P, const int64_t (&r)[NT], const bool (&ok)[NT], int ph,
+                                             const RhsState* S, const bool (&inner)[QT]) {
+    using VT = typename std::conditional<MIXED, float, double>::type;
+    const int Q = P.Q;
+    const float* dinv = P.amg->lv[0].dinv;
+    VT* pv = static_cast<VT*>(P.p[0]);
+    const VT* vv = static_cast<const VT*>(P.v[0]);
+    VT* rv = static_cast<VT*>(P.r);
+    // PRE_A: a = s, b = t, x, h1 = ph, h2 = sh (a pending step) or a = r; c = p, w = v.
+    // PRE_B: a = r, w = v.
+    float d0[NT];
+    VT a[NT][QT], b[NT][QT], c[NT][QT], w[NT][QT], x[NT][QT], h1[NT][QT], h2[NT][QT];
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+        d0[k] = ok[k] ? dinv[r[k]] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < QT; q++) {
+            a[k][q] = b[k][q] = c[k][q] = w[k][q] = x[k][q] = h1[k][q] = h2[k][q] = (VT)0;
+            if (!ok[k] || q >= Q) continue;
+            const int64_t e = r[k] * Q + q;
+            if (ph == P_PRE_A && S[q].pending) {
+                a[k][q] = static_cast<const VT*>(P.s)[e];
+                b[k][q] = static_cast<const VT*>(P.t)[e];
+                x[k][q] = static_cast<const VT*>(P.x)[e];
+                h1[k][q] = static_cast<const VT*>(P.ph)[e];
+                h2[k][q] = static_cast<const VT*>(P.sh)[e];
+            } else if (inner[q]) {
+                a[k][q] = rv[e];
+            }
+            if (inner[q]) {
+                w[k][q] = vv[e];
+                if (ph == P_PRE_A) c[k][q] = pv[e];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+        if (!ok[k]) continue;
+#pragma unroll
+        for (int q = 0; q < QT; q++) {
+            if (q >= Q) break;
+            const int64_t e = r[k] * Q + q;
+            if (ph == P_PRE_A) {
+                VT rn = a[k][q];
+                if (S[q].pending) {
+                    const VT om = (VT)S[q].omega;
+                    rn = a[k][q] - om * b[k][q];
+                    rv[e] = rn;
+                    static_cast<VT*>(P.x)[e] = x[k][q] + (VT)S[q].alpha * h1[k][q] + om * h2[k][q];
+                }
+                if (inner[q]) {
+                    const VT nv = rn + (VT)S[q].beta * (c[k][q] - (VT)S[q].omega * w[k][q]);
+                    pv[e] = nv;
+                    P.vy[0][e] = d0[k] * (float)nv;
+                }
+            } else if (inner[q]) {
+                const VT nv = a[k][q] - (VT)S[q].alpha * w[k][q];
+                static_cast<VT*>(P.s)[e] = nv;
+                P.vy[0][e] = d0[k] * (float)nv;
+            }
+        }
+    }
+}
+
 // A: v = A ph and (rh, v); B: t = A sh and (t, s), (t, t), (rh, s), (rh, t),
 // (s, s); from the staged slice (every lane of the warp calls).
 template <bool MIXED, int QT, typename Landed>
@@ -830,13 +954,14 @@ __host__ __device__ constexpr size_t stage_bytes_per_warp(int kmax) {
 // t + 256, ... in batches of kFinBatch whose loads are all issued before any
 // is added, each batch summed as a balanced pairwise tree, the batches in
 // order; then a butterfly over the warp and a pairwise tree over the 8 warps.
-// The dependent chain is log-depth (FP64 additions have a long latency here)
-// and costs one L2 round trip a batch.
+// The dependent chain is log-depth and costs one L2 round trip a batch; the
+// additions are F2 in the FP32 flow (see Part).
 template <bool MIXED, int QT, bool AMG>
 __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int slot, int cnt, const RhsState* S,
-                                                    double (&fin)[kThreads / 32][chan_count(AMG) * QT],
+                                                    Part<MIXED> (&fin)[kThreads / 32][chan_count(AMG) * QT],
                                                     double (&tot)[chan_count(AMG) * QT], int* last, const Ctl& ctl) {
     constexpr int NC = chan_count(AMG);
+    using PT = Part<MIXED>;
     const int nch = (AMG && ph == P_B) ? kChanAmg : kChan;  // the channels this step reduces
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     // the block's partial stores precede the barrier; thread 0's fence releases
@@ -851,7 +976,7 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
     }
     __syncthreads();
     if (*last) {
-        constexpr int kFinBatch = QT == 1 ? 16 : 8;
+        constexpr int kFinBatch = (QT == 1 && !MIXED) ? 16 : 8;
         const int nchunk = P.nchunk, Q = P.Q;
         // two channels (or right-hand sides) at a time: 2 x kFinBatch loads in flight
 #pragma unroll
@@ -859,31 +984,32 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
             const int e1 = e0 + 1;
             const bool on0 = e0 / QT < nch && e0 % QT < Q;                   // step-uniform
             const bool on1 = e1 < NC * QT && e1 / QT < nch && e1 % QT < Q;  // step-uniform
-            double acc0 = 0.0, acc1 = 0.0;
+            PT acc0 = part_zero<PT>(), acc1 = part_zero<PT>();
             if (on0 || on1) {
-                const double* b0 = &P.part[((int64_t)slot * NC + e0 / QT) * nchunk * Q + e0 % QT];
-                const double* b1 = &P.part[((int64_t)slot * NC + e1 / QT) * nchunk * Q + e1 % QT];
+                const PT* part = static_cast<const PT*>(P.part);
+                const PT* b0 = &part[((int64_t)slot * NC + e0 / QT) * nchunk * Q + e0 % QT];
+                const PT* b1 = &part[((int64_t)slot * NC + e1 / QT) * nchunk * Q + e1 % QT];
                 for (int l0 = tid; l0 < nchunk; l0 += kThreads * kFinBatch) {
-                    double v0[kFinBatch], v1[kFinBatch];
+                    PT v0[kFinBatch], v1[kFinBatch];
 #pragma unroll
                     for (int u = 0; u < kFinBatch; u++) {
                         const int l = l0 + u * kThreads;
-                        v0[u] = on0 && l < nchunk ? __ldcg(b0 + (int64_t)l * Q) : 0.0;
-                        v1[u] = on1 && l < nchunk ? __ldcg(b1 + (int64_t)l * Q) : 0.0;
+                        v0[u] = on0 && l < nchunk ? part_load(b0 + (int64_t)l * Q) : part_zero<PT>();
+                        v1[u] = on1 && l < nchunk ? part_load(b1 + (int64_t)l * Q) : part_zero<PT>();
                     }
 #pragma unroll
                     for (int w = 1; w < kFinBatch; w <<= 1)
 #pragma unroll
                         for (int u = 0; u < kFinBatch; u += 2 * w) {
-                            v0[u] += v0[u + w];
-                            v1[u] += v1[u + w];
+                            v0[u] = part_add(v0[u], v0[u + w]);
+                            v1[u] = part_add(v1[u], v1[u + w]);
                         }
-                    acc0 += v0[0];
-                    acc1 += v1[0];
+                    acc0 = part_add(acc0, v0[0]);
+                    acc1 = part_add(acc1, v1[0]);
                 }
             }
-            if (on0) acc0 = warp_sum(acc0);
-            if (on1) acc1 = warp_sum(acc1);
+            if (on0) acc0 = part_warp_sum(acc0);
+            if (on1) acc1 = part_warp_sum(acc1);
             if (lane == 0) {
                 fin[wid][e0] = acc0;
                 if (e1 < NC * QT) fin[wid][e1] = acc1;
@@ -892,9 +1018,10 @@ __device__ __forceinline__ void arrive_and_finalize(const Prob& P, int ph, int s
         __syncthreads();
         static_assert(kThreads / 32 == 8, "the warp tree below sums 8 warps");
         if (tid < NC * QT) {
-            const double* f = &fin[0][tid];
+            const PT* f = &fin[0][tid];
             constexpr int W = NC * QT;
-            tot[tid] = ((f[0] + f[W]) + (f[2 * W] + f[3 * W])) + ((f[4 * W] + f[5 * W]) + (f[6 * W] + f[7 * W]));
+            tot[tid] = part_value(part_add(part_add(part_add(f[0], f[W]), part_add(f[2 * W], f[3 * W])),
+                                           part_add(part_add(f[4 * W], f[5 * W]), part_add(f[6 * W], f[7 * W]))));
         }
         __syncthreads();
         if (tid < P.Q) {
@@ -941,9 +1068,9 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     constexpr int NC = chan_count(AMG);
     // about 5 KB of pending partials at most
     constexpr int kRedTiles = 80 / (NC * QT) > 16 ? 16 : (80 / (NC * QT) < 2 ? 2 : 80 / (NC * QT));
-    __shared__ double red[kRedTiles][kThreads / 32][NC * QT];
+    __shared__ Part<MIXED> red[kRedTiles][kThreads / 32][NC * QT];
     __shared__ int red_lc[kRedTiles];
-    __shared__ double fin[kThreads / 32][NC * QT];
+    __shared__ Part<MIXED> fin[kThreads / 32][NC * QT];
     __shared__ double tot[NC * QT];
     __shared__ int last;
     __shared__ float vagg[kThreads / kAmgAgg];  // a block's row residuals on a small level (agg_sum)
@@ -1051,11 +1178,13 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
             for (int e = tid; e < nred * NC * QT; e += kThreads) {
                 const int t = e / (NC * QT), j = e % (NC * QT);
                 if (j / QT >= nch) continue;
-                const double* rw = &red[t][0][j];
+                const Part<MIXED>* rw = &red[t][0][j];
                 constexpr int W = NC * QT;  // stride between warps
-                const double v = ((rw[0] + rw[W]) + (rw[2 * W] + rw[3 * W])) + ((rw[4 * W] + rw[5 * W]) + (rw[6 * W] + rw[7 * W]));
+                const Part<MIXED> v = part_add(part_add(part_add(rw[0], rw[W]), part_add(rw[2 * W], rw[3 * W])),
+                                               part_add(part_add(rw[4 * W], rw[5 * W]), part_add(rw[6 * W], rw[7 * W])));
                 const int ch = j / QT, q = j % QT;
-                if (q < P.Q) P.part[(((int64_t)slot * NC + ch) * P.nchunk + red_lc[t]) * P.Q + q] = v;
+                if (q < P.Q)
+                    static_cast<Part<MIXED>*>(P.part)[(((int64_t)slot * NC + ch) * P.nchunk + red_lc[t]) * P.Q + q] = v;
             }
             __syncthreads();
             nred = 0;
@@ -1140,6 +1269,45 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
         if (ph == ph_end && blockIdx.x == 0 && tid == 0 && ctl.cancel && *(const volatile int*)ctl.cancel != 0)
             *ctl.stop = 1;
         if (reduce) held = -1;  // the states were advanced at the arrivals
+        const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit,
+                                  !(ctl.withhold && blockIdx.x == 0 && bar_epoch == 0));
+        trace_step(ctl, (unsigned)ph);
+        return ok;
+    };
+
+    // PRE_A / PRE_B of the multigrid flow with one or two right-hand sides:
+    // up to NT of the block's tiles of one request at a time (amg_pre_rows), so
+    // their loads overlap; a request with a RESTART goes row by row (the fold of
+    // x into u).  The rows and their arithmetic are those of fine_phase.
+    auto pre_phase = [&](int ph) -> bool {
+        constexpr int NT = MIXED ? (QT == 1 ? 4 : 2) : (QT == 1 ? 2 : 1);  // operands in registers
+        const int G = (int)gridDim.x;
+        for (int c = blockIdx.x; c < tab.fine.nchunks;) {
+            const int ri = unit_req(tab, tab.fine, c);
+            if (ri != held) enter(ri, ph);
+            int n = 1;
+            while (n < NT && c + n * G < tab.fine.nchunks && unit_req(tab, tab.fine, c + n * G) == ri) n++;
+            if (!all_done) {
+                const Prob& P = sP;
+                const int base = unit_base(tab, tab.fine, ri);
+                if (any_restart) {
+                    for (int k = 0; k < n; k++) {
+                        const int64_t r = (int64_t)(c + k * G - base) * kCh + tid;
+                        if (r < P.n) amg_pre_row<MIXED, QT>(P, r, ph, S, inner, restart);
+                    }
+                } else {
+                    int64_t rows[NT];
+                    bool ok[NT];
+#pragma unroll
+                    for (int k = 0; k < NT; k++) {
+                        rows[k] = (int64_t)(c + k * G - base) * kCh + tid;
+                        ok[k] = k < n && rows[k] < P.n;
+                    }
+                    amg_pre_rows<MIXED, QT, NT>(P, rows, ok, ph, S, inner);
+                }
+            }
+            c += n * G;
+        }
         const bool ok = grid_sync(ctl.bar, bar_epoch, ctl.err, ctl.limit,
                                   !(ctl.withhold && blockIdx.x == 0 && bar_epoch == 0));
         trace_step(ctl, (unsigned)ph);
@@ -1295,8 +1463,12 @@ __global__ void __launch_bounds__(kThreads, QT <= 2 ? 3 : 2)
     for (int it = 0; it < iter_budget; ++it) {
         bool ok = true;
         if (AMG) {
-            ok = fine_phase(P_PRE_A) && vcycle(0) && fine_phase(P_A) && fine_phase(P_PRE_B) && vcycle(1) &&
-                 fine_phase(P_B);
+            if constexpr (QT <= 2)
+                ok = pre_phase(P_PRE_A) && vcycle(0) && fine_phase(P_A) && pre_phase(P_PRE_B) && vcycle(1) &&
+                     fine_phase(P_B);
+            else
+                ok = fine_phase(P_PRE_A) && vcycle(0) && fine_phase(P_A) && fine_phase(P_PRE_B) && vcycle(1) &&
+                     fine_phase(P_B);
         } else {
             // read after the last barrier of the previous iteration: identical in every block
             const bool pre_a = !MIXED || *(volatile int*)ctl.nrestart > 0;
