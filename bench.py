@@ -40,7 +40,7 @@ RTOL = 1e-8
 # DRAM bytes (read + write) per iteration of k_solve<1,1,1> on the bench workload
 # (N = 1,048,576, K = 20, multigrid, FP32 inner), from an ncu capture of the
 # current kernel; None until one is taken (the line then reports traffic null).
-KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = None
+KSOLVE_MIXED_AMG_DRAM_PER_ITERATION = 1.108e9  # 22.162 GB over a 20-iteration capture
 BATCH_MAXIT = 3000  # batched workload: iteration cap per cloud (see batched_measure)
 SERVED_REQUESTS, SERVED_RATE = 60, 20.0  # the served slice in the default line (below saturation)
 WORKLOAD = ("random unit sphere N=1,048,576 (normalised PCG64(0) Gaussian rows), K=20, delta = mean distance to "
