@@ -531,7 +531,9 @@ mvgd_status mvgd_request_poll(void *const *reqs, int32_t count, int32_t *done, m
  * Step trace (diagnostics; no counterpart in the paper).  When enabled, the
  * persistent solver stamps the device clock (ns) after every grid-wide step:
  * entry = code << 48 | (time & 2^48-1), code = Krylov phase 0..4 (PRE_A, A,
- * PRE_B, B, C), or 0x1000 | side << 8 | kind << 4 | level for a multigrid step
+ * PRE_B, B, C; the multigrid flow has no C step: its B ends an iteration and
+ * the next PRE_A forms the new residual), or
+ * 0x1000 | side << 8 | kind << 4 | level for a multigrid step
  * (side 0: the cycle on p, 1: on s; kind 0 down, 1 coarsest, 2 up).  Process-
  * wide, one device; entries past 65,536 wrap.  Both calls synchronise.
  * mvgd_trace_enable: on != 0 clears the trace and turns it on for launches
