@@ -255,10 +255,11 @@ __host__ __device__ constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 *
 
 // Tile partials and their sums: F2 (double-float on the FP32 pipe) in the
 // FP32 flow, double in the FP64 one.  One SM sums a request's thousands of
-// partials in each reducing step; GB300 issues FP64 additions at 2 lanes a
-// clock an SM (a warp instruction every 16 clocks, 63 clocks of latency), so in
-// FP64 that sum alone took about 1 us a channel at 1M rows, and F2 additions
-// (eight FP32 operations) take a fraction of it with about 48 bits.  The F2
+// partials in each reducing step.  GB300's FP64 rate (1.25 TFLOP/s nominal)
+// is about two FP64 lanes a clock an SM, a warp instruction every 16 clocks,
+// with 63 clocks of latency (measured), so in FP64 that sum alone took about
+// 1 us a channel at 1M rows; F2 additions (eight FP32 operations) take a
+// fraction of it with about 48 bits.  The F2
 // range is FP32's: the FP32 flow's squared residual norms stay below 3.4e38
 // (||f|| below about 1.8e19) or the step reports a non-finite residual.
 template <bool MIXED>
